@@ -1,0 +1,230 @@
+/*
+ * bbmd.h -- C ABI of the GB300 hot path of the short-range molecular-dynamics method of
+ * Allsopp, Ruocco & Fratalocchi (BBMD): cell binning, Verlet neighbour list, truncated
+ * Lennard-Jones / soft-sphere pair forces of a two-species mixture in a periodic box,
+ * velocity Verlet with an optional Nose-Hoover thermostat, device reductions and the
+ * observables of the paper's glass study.
+ *
+ * The paper defines the problem, not an API (Sec. 2.1 potentials, Sec. 2.2 cell search,
+ * Sec. 2.3.2 velocity Verlet, Sec. 3 canonical benchmark runs, Sec. 4 g(r)); these calls
+ * follow that statement of the problem.
+ *
+ * Conventions for every call
+ *   - Host arrays are caller-owned and only read or written during the call.  Positions,
+ *     velocities and forces on the host are row-major (n, 3) doubles in particle-id order
+ *     (id = index in the arrays given to bbmd_create).  Species labels are uint8 0 (A)
+ *     or 1 (B).
+ *   - Device memory is owned by the handle and obtained through the caller's allocator
+ *     (bbmd_alloc) or cudaMalloc when it is NULL; bbmd_destroy returns all of it.
+ *   - Work is enqueued on the CUDA stream given to bbmd_create (NULL = legacy default).
+ *     bbmd_step returns after enqueueing; every call that returns host data synchronises
+ *     that stream.
+ *   - Errors are returned as bbmd_status codes, never by abort or exit.  A device-side
+ *     status word (list overflow, non-finite force, velocity overflow) is sticky and is
+ *     reported by the next synchronising call.  bbmd_last_error gives a message.
+ *   - A handle is not thread-safe.
+ *
+ * State representation (the exact rules the test oracle implements independently)
+ *   - Positions are held as signed 64-bit integers in units of 2^-k with
+ *     k = 61 - floor(log2(max box side)); box sides must be >= 1 and are exact integers
+ *     in that unit.  Input positions are quantised as round-half-even(x * 2^k) and
+ *     reduced modulo the box into [0, L).  Velocities are 64-bit integers in units of
+ *     2^-52 (|v| < 2048).
+ *   - Cells: nc = floor(L / rcell) per axis, side D = floor(L*2^k / nc) truncated to 24
+ *     significant bits (nc lowered while D*2^-k < rcell); cell a = min(nc-1, x_fix / D).
+ *     rcell = max rcut + skin.  Fewer than 3 cells on an axis -> BBMD_ERR_BOX_TOO_SMALL.
+ *   - Pair distance: dx = x_j - x_i as an integer, reduced to the minimum image, rounded
+ *     once to double, scaled by 2^-k; r^2 = (dx*dx + dy*dy) + dz*dz in IEEE double with
+ *     no fused multiply-add.  Cutoff and list decisions use this r^2 with strict "<":
+ *     a pair interacts iff r^2 < rcut_ab^2; j is in the Verlet list of i iff
+ *     r^2 < (rcut_ab + skin)^2.  Mixed precision evaluates r^2 in FP32 and re-tests in
+ *     FP64 by this rule whenever it lies within a relative 1e-5 of the threshold, so
+ *     both decisions are exact.
+ */
+#ifndef BBMD_H
+#define BBMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BBMD_OK = 0,
+    BBMD_ERR_ARG = 1,             /* invalid argument                                       */
+    BBMD_ERR_BOX_TOO_SMALL = 2,   /* fewer than 3 cells per axis                            */
+    BBMD_ERR_OOM = 3,             /* the allocator returned NULL                            */
+    BBMD_ERR_CUDA = 4,            /* a CUDA runtime call failed                             */
+    BBMD_ERR_LIST_OVERFLOW = 5,   /* a Verlet list or a staged stencil exceeded capacity    */
+    BBMD_ERR_NUMERIC = 6,         /* non-finite force or |v| beyond the fixed-point range   */
+    BBMD_ERR_TIMEOUT = 7,         /* a bounded device wait gave up                          */
+    BBMD_ERR_STATE = 8            /* call not valid in the handle's current state           */
+} bbmd_status;
+
+enum { BBMD_POT_LJ = 0, BBMD_POT_SOFT = 1 };                 /* Eq. lj0, Eq. sc0          */
+enum { BBMD_SHIFT_NONE = 0, BBMD_SHIFT_ENERGY = 1,            /* plain cut; V - V(rc)      */
+       BBMD_SHIFT_FORCE = 2 };                                /* Eq. mod0 (shifted force)  */
+enum { BBMD_PREC_MIXED = 0, BBMD_PREC_FP64 = 1 };             /* FP32 pair math / FP64     */
+enum { BBMD_NBR_VERLET = 0, BBMD_NBR_CELL = 1 };              /* stored list / on the fly  */
+enum { BBMD_THERMO_NVE = 0, BBMD_THERMO_NH = 1 };
+
+/* Pair model and neighbour-search parameters.
+ * eps, sigma, rcut: [a][b] tables (must be symmetric); mass[a] > 0.
+ * skin: Verlet skin (>= 0); the list is rebuilt when some particle has moved more than
+ *   skin/2 since the last build (Verlet mode) or, in cell mode, when it has left the
+ *   margin skin/2 that the cells carry.
+ * list_capacity: maximum list entries per particle (0 = 160; rounded up to 8).
+ * stencil_capacity: maximum particles in the 27 cells around one cell (0 = from density). */
+typedef struct {
+    int32_t potential;
+    int32_t shift;
+    int32_t precision;
+    int32_t nbr_mode;
+    double eps[2][2];
+    double sigma[2][2];
+    double rcut[2][2];
+    double mass[2];
+    double skin;
+    int32_t list_capacity;
+    int32_t stencil_capacity;
+} bbmd_params;
+
+/* Thermostat of one bbmd_step call.  NVE, or Nose-Hoover with one friction variable xi,
+ * Q = g T tau^2 (g = 3n - 3), target T_k = T_start + (T_end - T_start) * k / nsteps for
+ * step k = 0 .. nsteps-1 of the call (a linear ramp; constant when T_start == T_end).
+ * Each step is NH-half, kick, drift, force, kick, NH-half (Trotter splitting). */
+typedef struct {
+    int32_t kind;
+    double T_start;
+    double T_end;
+    double tau;
+} bbmd_thermostat;
+
+/* Device allocator: alloc returns a device pointer (NULL on failure); free releases it. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* ctx;
+} bbmd_alloc;
+
+typedef struct bbmd_sim bbmd_sim;
+
+/* bbmd_observe mask bits */
+enum {
+    BBMD_OBS_ENERGY = 1u,    /* kinetic, potential, temperature, conserved quantity     */
+    BBMD_OBS_VIRIAL = 2u,    /* virial W = sum_{i<j} r_ij . F_ij and pressure            */
+    BBMD_OBS_MOMENTUM = 4u,  /* total momentum                                          */
+    BBMD_OBS_GR = 8u,        /* partial g_ab(r) (Sec. 4)                                */
+    BBMD_OBS_MSD = 16u,      /* mean-square displacement per species since SET_REF      */
+    BBMD_OBS_FS = 32u,       /* self-intermediate scattering F_s(k, t) since SET_REF    */
+    BBMD_OBS_SET_REF = 64u   /* store the current unwrapped positions as the reference  */
+};
+
+typedef struct {
+    int32_t nbins;   /* g(r) bins (0 = 500)  */
+    double rmax;     /* g(r) range (0 = 5.0) */
+    double k;        /* F_s wave number (0 = 7.25) */
+} bbmd_obs_args;
+
+/* Results of bbmd_observe.  gr_counts[(a*2+b)*nbins + q] counts ordered pairs (i in a,
+ * j in b, j != i) with floor(r/dr) = q, dr = rmax/nbins, r from the exact r^2 rule;
+ * gr[...] = V n_ab / (N_a N'_b (4 pi/3)(r_{q+1}^3 - r_q^3)), N'_b = N_b - (a == b).
+ * Both pointers are caller-owned (4*nbins entries) and may be NULL. */
+typedef struct {
+    double ke, pe, virial, pressure, temperature;
+    double momentum[3];
+    double xi, eta, conserved;  /* NH variables; conserved = K + U + Q xi^2/2 + g T eta   */
+    int64_t step;               /* steps taken since creation                           */
+    int64_t n_rebuilds;         /* list / cell rebuilds since creation                  */
+    uint64_t* gr_counts;
+    double* gr;
+    double msd[2];
+    double fs[2];
+} bbmd_obs;
+
+/* Static facts of a handle. */
+typedef struct {
+    int64_t n;
+    int32_t fix_exponent;    /* k of the position unit 2^-k                */
+    int32_t nc[3];           /* cells per axis                             */
+    int64_t cell_side_fix[3];/* D per axis in units of 2^-k                */
+    int32_t list_capacity;
+    int32_t stencil_capacity;
+    int64_t device_bytes;    /* device memory held by the handle           */
+} bbmd_info;
+
+/* Create a system of n particles in a periodic box (Sec. 2).
+ * box[3]: sides (>= 1).  species: n labels (host, required).
+ * pos: n x 3 host positions, or NULL for the FCC lattice of 4 m^3 sites (n must equal
+ *   4 m^3) with site i = 4 (ix + m (iy + m iz)) + b at ((ix,iy,iz) + basis_b + 1/4) L/m.
+ * vel: n x 3 host velocities, or NULL for Maxwell-Boltzmann velocities at T0 drawn from
+ *   the counter-based SplitMix64/Box-Muller generator under seed (net momentum removed,
+ *   then scaled to 2K/(3n-3) = T0).
+ * stream: a cudaStream_t (NULL = legacy default stream).  alloc: NULL = cudaMalloc.
+ * On success *out receives the handle, the first list is built and the forces of the
+ * initial positions are computed. */
+/* Non-finite input positions or velocities are rejected with BBMD_ERR_ARG. */
+bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3],
+                        const uint8_t* species, const double* pos, const double* vel,
+                        double T0, uint64_t seed, void* stream, const bbmd_alloc* alloc,
+                        bbmd_sim** out);
+
+/* Release all device memory of the handle (NULL is ignored). */
+void bbmd_destroy(bbmd_sim* sim);
+
+/* Advance nsteps velocity-Verlet steps of size dt (Sec. 2.3.2) under the thermostat
+ * (NULL = NVE).  Asynchronous: returns after enqueueing on the handle's stream.  The list
+ * is rebuilt on the device when needed, without a host round trip. */
+bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* thermo);
+
+/* Measure the observables selected by mask at the current state (synchronising).  args may
+ * be NULL for the defaults.  out->gr_counts / out->gr are filled when non-NULL and GR is
+ * set. */
+bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args,
+                         bbmd_obs* out);
+
+/* Steepest descent x += h F, h = min(hmax, dmax / max_i |F_i|), nsteps times; the forces
+ * of the final positions are left valid.  Velocities are untouched. */
+bbmd_status bbmd_minimize(bbmd_sim* sim, int64_t nsteps, double hmax, double dmax);
+
+/* Copy the state to host arrays in id order (each may be NULL): positions wrapped into
+ * [0, L) (n x 3), velocities (n x 3), image counters (n x 3, box crossings since creation).
+ * Synchronising. */
+bbmd_status bbmd_get_state(bbmd_sim* sim, double* pos, double* vel, int32_t* image);
+
+/* Replace positions (n x 3, quantised as in bbmd_create), velocities (n x 3) and image
+ * counters (n x 3, NULL = zeros) from host arrays in id order.  Species are kept.  The
+ * list is rebuilt and forces recomputed; the thermostat variables are kept. */
+bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
+                           const int32_t* image);
+
+/* Forces of the current positions (n x 3, id order) and, when u is non-NULL, per-particle
+ * potential energy (half of each pair energy).  Recomputes on the device; synchronising. */
+bbmd_status bbmd_get_forces(bbmd_sim* sim, double* F, double* u);
+
+/* Cell of each particle at the last rebuild (n entries, id order):
+ * (az * ncy + ay) * ncx + ax.  Synchronising. */
+bbmd_status bbmd_get_cells(bbmd_sim* sim, int64_t* cell);
+
+/* Current Verlet list as sets of ids.  ids: the m particle ids to report (NULL = all n,
+ * in id order).  offsets[m+1] (or [n+1]) receives the prefix of the list lengths and, when
+ * nbr is non-NULL, nbr[offsets[s] .. offsets[s+1]) the ascending ids of the list of the
+ * s-th requested particle (cap entries available; BBMD_ERR_ARG if too small).  Verlet mode
+ * only (BBMD_ERR_STATE otherwise).  Synchronising. */
+bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int64_t* offsets,
+                               int64_t* nbr, int64_t cap);
+
+/* Force a rebuild (binning, reorder and list) at the current positions. */
+bbmd_status bbmd_rebuild(bbmd_sim* sim);
+
+bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info);
+
+/* Message of the last failed call on this handle ("" if none). */
+const char* bbmd_last_error(const bbmd_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

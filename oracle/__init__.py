@@ -106,6 +106,10 @@ def lib():
         L.orc_neighbors_brute.restype = None
         L.orc_neighbors_cells.argtypes = [i64, pd, i32, pi64, pu8, pd, d, pi64, pi64]
         L.orc_neighbors_cells.restype = i32
+        L.orc_forces_subset.argtypes = [i64, pd, pu8, pd, pP, i64, pi64, pd, pd]
+        L.orc_forces_subset.restype = i32
+        L.orc_neighbors_subset.argtypes = [i64, pd, i32, pi64, pu8, pd, d, i64, pi64, pi64, pi64]
+        L.orc_neighbors_subset.restype = i32
         L.orc_kinetic.argtypes = [i64, pu8, pd, pP, pd]
         L.orc_kinetic.restype = d
         L.orc_md_run.argtypes = [i64, pd, pu8, pP, pd, pd, C.POINTER(C.c_int32), pd, i32,
@@ -171,6 +175,36 @@ def forces(pos, species, L, p: Params, method: str = "brute"):
         if rc != 0:
             raise ValueError("box too small for the cell search")
     return F, u, W.value, PE.value
+
+
+def forces_subset(pos, species, L, p: Params, idx):
+    """Forces (m,3) and energies (m,) of particles idx only (cell search, Sec. 2.2)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    sp = np.ascontiguousarray(species, dtype=np.uint8)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    F = np.zeros((idx.size, 3))
+    u = np.zeros(idx.size)
+    if lib().orc_forces_subset(pos.shape[0], _dp(_box(L)), _u8p(sp), _dp(pos), C.byref(p),
+                               idx.size, _ip(idx), _dp(F), _dp(u)) != 0:
+        raise ValueError("box too small for the cell search")
+    return F, u
+
+
+def neighbors_subset(xfix, species, L, k, R2, idx, rcell):
+    xfix = np.ascontiguousarray(xfix, dtype=np.int64)
+    sp = np.ascontiguousarray(species, dtype=np.uint8)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    R2 = np.ascontiguousarray(R2, dtype=np.float64)
+    off = np.zeros(idx.size + 1, dtype=np.int64)
+    Lb = _box(L)
+    L_ = lib()
+    if L_.orc_neighbors_subset(xfix.shape[0], _dp(Lb), k, _ip(xfix), _u8p(sp), _dp(R2), rcell,
+                               idx.size, _ip(idx), _ip(off), None) != 0:
+        raise ValueError("box too small for the cell grid")
+    nbr = np.zeros(max(int(off[-1]), 1), dtype=np.int64)
+    L_.orc_neighbors_subset(xfix.shape[0], _dp(Lb), k, _ip(xfix), _u8p(sp), _dp(R2), rcell,
+                            idx.size, _ip(idx), _ip(off), _ip(nbr))
+    return off, nbr[: int(off[-1])]
 
 
 def fix_exponent(L) -> int:

@@ -175,6 +175,57 @@ int orc_forces_cells(int64_t n, const double L[3], const uint8_t* species, const
     return 0;
 }
 
+int orc_forces_subset(int64_t n, const double L[3], const uint8_t* species, const double* pos,
+                      const orc_params* p, int64_t m, const int64_t* idx, double* F, double* u) {
+    double rc = max_rcut(p);
+    int64_t nc[3];
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int64_t)floor(L[k] / rc);
+        if (nc[k] < 3) return -1;
+    }
+    int64_t ncell = nc[0] * nc[1] * nc[2];
+    int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t a0 = plain_cell(pos[3 * i], L[0], nc[0]);
+        int64_t a1 = plain_cell(pos[3 * i + 1], L[1], nc[1]);
+        int64_t a2 = plain_cell(pos[3 * i + 2], L[2], nc[2]);
+        int64_t c = (a2 * nc[1] + a1) * nc[0] + a0;
+        next[i] = head[c];
+        head[c] = i;
+    }
+    for (int64_t s = 0; s < m; ++s) {
+        int64_t i = idx[s];
+        double f[3] = {0.0, 0.0, 0.0}, ui = 0.0;
+        int64_t a[3];
+        for (int k = 0; k < 3; ++k) a[k] = plain_cell(pos[3 * i + k], L[k], nc[k]);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t bx = (a[0] + dx + nc[0]) % nc[0];
+                    int64_t by = (a[1] + dy + nc[1]) % nc[1];
+                    int64_t bz = (a[2] + dz + nc[2]) % nc[2];
+                    for (int64_t j = head[(bz * nc[1] + by) * nc[0] + bx]; j >= 0; j = next[j]) {
+                        if (j == i) continue;
+                        double d[3];
+                        for (int k = 0; k < 3; ++k)
+                            d[k] = min_image(pos[3 * j + k] - pos[3 * i + k], L[k]);
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        double V, fr;
+                        if (!orc_pair(p, species[i], species[j], r2, &V, &fr)) continue;
+                        for (int k = 0; k < 3; ++k) f[k] -= fr * d[k];
+                        ui += 0.5 * V;
+                    }
+                }
+        for (int k = 0; k < 3; ++k) F[3 * s + k] = f[k];
+        if (u) u[s] = ui;
+    }
+    free(head);
+    free(next);
+    return 0;
+}
+
 /* ---------------------------------------------------------------------------------- */
 /* fixed-point positions, cells, neighbour sets                                        */
 /* ---------------------------------------------------------------------------------- */
@@ -325,6 +376,53 @@ int orc_neighbors_cells(int64_t n, const double L[3], int k, const int64_t* xfix
         if (nbr) qsort(nbr + start, (size_t)(pos - start), sizeof(int64_t), cmp_i64);
     }
     offsets[n] = pos;
+    free(cell);
+    free(head);
+    free(next);
+    return 0;
+}
+
+int orc_neighbors_subset(int64_t n, const double L[3], int k, const int64_t* xfix,
+                         const uint8_t* species, const double R2[2][2], double rcell, int64_t m,
+                         const int64_t* idx, int64_t* offsets, int64_t* nbr) {
+    int64_t nc[3], D[3], Lf[3];
+    if (orc_cell_grid(L, k, rcell, nc, D) != 0) return -1;
+    lfix_of(L, k, Lf);
+    int64_t ncell = nc[0] * nc[1] * nc[2];
+    int64_t* cell = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    orc_bin(n, xfix, nc, D, cell);
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = n - 1; i >= 0; --i) {
+        next[i] = head[cell[i]];
+        head[cell[i]] = i;
+    }
+    int64_t pos = 0;
+    for (int64_t s = 0; s < m; ++s) {
+        int64_t i = idx[s];
+        offsets[s] = pos;
+        int64_t c = cell[i];
+        int64_t ax = c % nc[0], ay = (c / nc[0]) % nc[1], az = c / (nc[0] * nc[1]);
+        int64_t start = pos;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t bx = (ax + dx + nc[0]) % nc[0];
+                    int64_t by = (ay + dy + nc[1]) % nc[1];
+                    int64_t bz = (az + dz + nc[2]) % nc[2];
+                    for (int64_t j = head[(bz * nc[1] + by) * nc[0] + bx]; j >= 0; j = next[j]) {
+                        if (j == i) continue;
+                        double r2 = orc_r2_fixed(xfix + 3 * i, xfix + 3 * j, Lf, k);
+                        if (r2 < R2[species[i]][species[j]]) {
+                            if (nbr) nbr[pos] = j;
+                            ++pos;
+                        }
+                    }
+                }
+        if (nbr) qsort(nbr + start, (size_t)(pos - start), sizeof(int64_t), cmp_i64);
+    }
+    offsets[m] = pos;
     free(cell);
     free(head);
     free(next);

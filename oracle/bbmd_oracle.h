@@ -69,6 +69,13 @@ void orc_forces_brute(int64_t n, const double L[3], const uint8_t* species, cons
 int orc_forces_cells(int64_t n, const double L[3], const uint8_t* species, const double* pos,
                      const orc_params* p, double* F, double* u, double* W, double* PE);
 
+/* Forces, per-particle energy and virial share of the m particles idx[] only, by the
+ * linked-cell search of Sec. 2.2 (both members of every pair visited, no Newton's third
+ * law): F[3m], u[m] (may be NULL).  For spot checks of very large systems.  Returns -1
+ * when the box holds fewer than 3 cells per axis. */
+int orc_forces_subset(int64_t n, const double L[3], const uint8_t* species, const double* pos,
+                      const orc_params* p, int64_t m, const int64_t* idx, double* F, double* u);
+
 /* ---- fixed-point positions, cells and neighbour sets --------------------------------- */
 /* Unit exponent k: positions are held as integers in units of 2^-k, k = 61 - floor(log2
  * max L).  Returns -1 if some L < 1. */
@@ -94,6 +101,11 @@ void orc_neighbors_brute(int64_t n, const double L[3], int k, const int64_t* xfi
 int orc_neighbors_cells(int64_t n, const double L[3], int k, const int64_t* xfix,
                         const uint8_t* species, const double R2[2][2], double rcell,
                         int64_t* offsets, int64_t* nbr);
+
+/* Neighbour sets of the m particles idx[] only (exact rule, cell grid with rcell). */
+int orc_neighbors_subset(int64_t n, const double L[3], int k, const int64_t* xfix,
+                         const uint8_t* species, const double R2[2][2], double rcell, int64_t m,
+                         const int64_t* idx, int64_t* offsets, int64_t* nbr);
 
 /* ---- integration (Sec. 2.3.2, velocity Verlet; canonical runs, Sec. 3) ------------- */
 /* Kinetic energy sum m v^2 / 2 and momentum sum m v. */

@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libbbmd (include/bbmd.h): the same entry points, argument
+marshalling only.  Every step of the hot path runs in the CUDA library; there is no CPU
+fallback -- loading fails loudly when the library has not been built.
+
+PyTorch supplies device memory (its caching allocator, passed as a bbmd_alloc) and the
+CUDA stream; both are optional.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbbmd.so")
+
+BBMD_OK = 0
+ERRORS = {
+    1: "BBMD_ERR_ARG", 2: "BBMD_ERR_BOX_TOO_SMALL", 3: "BBMD_ERR_OOM", 4: "BBMD_ERR_CUDA",
+    5: "BBMD_ERR_LIST_OVERFLOW", 6: "BBMD_ERR_NUMERIC", 7: "BBMD_ERR_TIMEOUT", 8: "BBMD_ERR_STATE",
+}
+POT_LJ, POT_SOFT = 0, 1
+SHIFT_NONE, SHIFT_ENERGY, SHIFT_FORCE = 0, 1, 2
+PREC_MIXED, PREC_FP64 = 0, 1
+NBR_VERLET, NBR_CELL = 0, 1
+THERMO_NVE, THERMO_NH = 0, 1
+OBS_ENERGY, OBS_VIRIAL, OBS_MOMENTUM, OBS_GR, OBS_MSD, OBS_FS, OBS_SET_REF = 1, 2, 4, 8, 16, 32, 64
+
+
+class BBMDError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bbmd_params(C.Structure):
+    _fields_ = [
+        ("potential", C.c_int32), ("shift", C.c_int32), ("precision", C.c_int32),
+        ("nbr_mode", C.c_int32),
+        ("eps", (C.c_double * 2) * 2), ("sigma", (C.c_double * 2) * 2),
+        ("rcut", (C.c_double * 2) * 2), ("mass", C.c_double * 2), ("skin", C.c_double),
+        ("list_capacity", C.c_int32), ("stencil_capacity", C.c_int32),
+    ]
+
+
+class bbmd_thermostat(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("T_start", C.c_double), ("T_end", C.c_double),
+                ("tau", C.c_double)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class bbmd_alloc(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
+class bbmd_obs_args(C.Structure):
+    _fields_ = [("nbins", C.c_int32), ("rmax", C.c_double), ("k", C.c_double)]
+
+
+class bbmd_obs(C.Structure):
+    _fields_ = [
+        ("ke", C.c_double), ("pe", C.c_double), ("virial", C.c_double), ("pressure", C.c_double),
+        ("temperature", C.c_double), ("momentum", C.c_double * 3), ("xi", C.c_double),
+        ("eta", C.c_double), ("conserved", C.c_double), ("step", C.c_int64),
+        ("n_rebuilds", C.c_int64), ("gr_counts", C.POINTER(C.c_uint64)),
+        ("gr", C.POINTER(C.c_double)), ("msd", C.c_double * 2), ("fs", C.c_double * 2),
+    ]
+
+
+class bbmd_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("fix_exponent", C.c_int32), ("nc", C.c_int32 * 3),
+                ("cell_side_fix", C.c_int64 * 3), ("list_capacity", C.c_int32),
+                ("stencil_capacity", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_observe", "bbmd_minimize",
+           "bbmd_get_state", "bbmd_set_state", "bbmd_get_forces", "bbmd_get_cells",
+           "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libbbmd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbbmd.so not found at {path}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(path)
+    P = C.POINTER
+    vp, i64, d = C.c_void_p, C.c_int64, C.c_double
+    L.bbmd_create.argtypes = [P(bbmd_params), i64, P(d), P(C.c_uint8), P(d), P(d), d, C.c_uint64,
+                              vp, P(bbmd_alloc), P(vp)]
+    L.bbmd_create.restype = C.c_int
+    L.bbmd_destroy.argtypes = [vp]
+    L.bbmd_destroy.restype = None
+    L.bbmd_step.argtypes = [vp, i64, d, P(bbmd_thermostat)]
+    L.bbmd_step.restype = C.c_int
+    L.bbmd_observe.argtypes = [vp, C.c_uint32, P(bbmd_obs_args), P(bbmd_obs)]
+    L.bbmd_observe.restype = C.c_int
+    L.bbmd_minimize.argtypes = [vp, i64, d, d]
+    L.bbmd_minimize.restype = C.c_int
+    L.bbmd_get_state.argtypes = [vp, P(d), P(d), P(C.c_int32)]
+    L.bbmd_get_state.restype = C.c_int
+    L.bbmd_set_state.argtypes = [vp, P(d), P(d), P(C.c_int32)]
+    L.bbmd_set_state.restype = C.c_int
+    L.bbmd_get_forces.argtypes = [vp, P(d), P(d)]
+    L.bbmd_get_forces.restype = C.c_int
+    L.bbmd_get_cells.argtypes = [vp, P(i64)]
+    L.bbmd_get_cells.restype = C.c_int
+    L.bbmd_get_neighbors.argtypes = [vp, P(i64), i64, P(i64), P(i64), i64]
+    L.bbmd_get_neighbors.restype = C.c_int
+    L.bbmd_rebuild.argtypes = [vp]
+    L.bbmd_rebuild.restype = C.c_int
+    L.bbmd_get_info.argtypes = [vp, P(bbmd_info)]
+    L.bbmd_get_info.restype = C.c_int
+    L.bbmd_last_error.argtypes = [vp]
+    L.bbmd_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(h, rc):
+    if rc != BBMD_OK:
+        msg = load().bbmd_last_error(h).decode() if h else ""
+        raise BBMDError(rc, msg)
+
+
+def ka_params(potential=POT_LJ, shift=SHIFT_ENERGY, precision=PREC_MIXED, nbr_mode=NBR_VERLET,
+              skin=0.3, rc_factor=2.5, mass=(1.0, 1.0), list_capacity=0, stencil_capacity=0):
+    """Parameters of the binary mixture of the paper's benchmark suite (Sec. 3):
+    eps_AA=1, eps_AB=1.5, eps_BB=0.5, sigma_AA=1, sigma_AB=0.8, sigma_BB=0.88, m=1."""
+    p = bbmd_params()
+    p.potential, p.shift, p.precision, p.nbr_mode = potential, shift, precision, nbr_mode
+    eps = ((1.0, 1.5), (1.5, 0.5))
+    sig = ((1.0, 0.8), (0.8, 0.88))
+    for a in range(2):
+        for b in range(2):
+            p.eps[a][b] = eps[a][b]
+            p.sigma[a][b] = sig[a][b]
+            p.rcut[a][b] = rc_factor * sig[a][b]
+    p.mass[0], p.mass[1] = mass
+    p.skin = skin
+    p.list_capacity = list_capacity
+    p.stencil_capacity = stencil_capacity
+    return p
+
+
+def torch_allocator(device=None):
+    """bbmd_alloc backed by torch's CUDA caching allocator (keep the returned tuple alive)."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    a = bbmd_alloc(fa, ff, None)
+    return a, (fa, ff)
+
+
+class Sim:
+    """Owner of one bbmd_sim handle; methods map one-to-one to the C entry points."""
+
+    def __init__(self, params, n, box, species, pos=None, vel=None, T0=0.0, seed=0,
+                 stream=None, use_torch_allocator=False):
+        L = load()
+        box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64), (3,)))
+        sp = np.ascontiguousarray(species, dtype=np.uint8)
+        if sp.shape != (n,):
+            raise ValueError("species must have n entries")
+        pos = None if pos is None else np.ascontiguousarray(pos, dtype=np.float64).reshape(n, 3)
+        vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64).reshape(n, 3)
+        self._keep = None
+        alloc = None
+        if use_torch_allocator:
+            alloc, self._keep = torch_allocator()
+        h = C.c_void_p()
+        stream_ptr = None if stream is None else C.c_void_p(int(stream))
+        rc = L.bbmd_create(C.byref(params), int(n), _dp(box),
+                           sp.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(pos), _dp(vel), float(T0),
+                           C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), stream_ptr,
+                           C.byref(alloc) if alloc is not None else None, C.byref(h))
+        if rc != BBMD_OK:
+            raise BBMDError(rc, "bbmd_create")
+        self.h = h
+        self.n = int(n)
+        self.box = box
+        self.params = params
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bbmd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps, dt, thermostat=None):
+        th = None
+        if thermostat is not None:
+            kind, T0, T1, tau = thermostat
+            th = bbmd_thermostat(kind, T0, T1, tau)
+        _check(self.h, load().bbmd_step(self.h, int(nsteps), float(dt),
+                                        C.byref(th) if th is not None else None))
+
+    def observe(self, mask, nbins=500, rmax=5.0, k=7.25):
+        o = bbmd_obs()
+        counts = g = None
+        if mask & OBS_GR:
+            counts = np.zeros((2, 2, nbins), dtype=np.uint64)
+            g = np.zeros((2, 2, nbins))
+            o.gr_counts = counts.ctypes.data_as(C.POINTER(C.c_uint64))
+            o.gr = _dp(g)
+        args = bbmd_obs_args(nbins, rmax, k)
+        _check(self.h, load().bbmd_observe(self.h, mask, C.byref(args), C.byref(o)))
+        res = {f: getattr(o, f) for f in ("ke", "pe", "virial", "pressure", "temperature", "xi",
+                                          "eta", "conserved", "step", "n_rebuilds")}
+        res["momentum"] = np.array(o.momentum[:])
+        res["msd"] = np.array(o.msd[:])
+        res["fs"] = np.array(o.fs[:])
+        if counts is not None:
+            res["gr_counts"] = counts
+            res["gr"] = g
+        return res
+
+    def minimize(self, nsteps, hmax=1e-3, dmax=0.05):
+        _check(self.h, load().bbmd_minimize(self.h, int(nsteps), float(hmax), float(dmax)))
+
+    def get_state(self):
+        pos = np.zeros((self.n, 3))
+        vel = np.zeros((self.n, 3))
+        img = np.zeros((self.n, 3), dtype=np.int32)
+        _check(self.h, load().bbmd_get_state(self.h, _dp(pos), _dp(vel),
+                                             img.ctypes.data_as(C.POINTER(C.c_int32))))
+        return pos, vel, img
+
+    def set_state(self, pos, vel, image=None):
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n, 3)
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(self.n, 3)
+        ip = None
+        if image is not None:
+            image = np.ascontiguousarray(image, dtype=np.int32).reshape(self.n, 3)
+            ip = image.ctypes.data_as(C.POINTER(C.c_int32))
+        _check(self.h, load().bbmd_set_state(self.h, _dp(pos), _dp(vel), ip))
+
+    def get_forces(self, energies=False):
+        F = np.zeros((self.n, 3))
+        u = np.zeros(self.n) if energies else None
+        _check(self.h, load().bbmd_get_forces(self.h, _dp(F), _dp(u)))
+        return (F, u) if energies else F
+
+    def get_cells(self):
+        c = np.zeros(self.n, dtype=np.int64)
+        _check(self.h, load().bbmd_get_cells(self.h, c.ctypes.data_as(C.POINTER(C.c_int64))))
+        return c
+
+    def get_neighbors(self, ids=None):
+        """Verlet lists as id sets: (offsets, nbr) for all particles (id order) or for ids."""
+        L = load()
+        P = C.POINTER(C.c_int64)
+        if ids is None:
+            m, ip = self.n, None
+        else:
+            ids = np.ascontiguousarray(ids, dtype=np.int64)
+            m, ip = ids.size, ids.ctypes.data_as(P)
+        off = np.zeros(m + 1, dtype=np.int64)
+        _check(self.h, L.bbmd_get_neighbors(self.h, ip, m, off.ctypes.data_as(P), None, 0))
+        nbr = np.zeros(max(int(off[-1]), 1), dtype=np.int64)
+        _check(self.h, L.bbmd_get_neighbors(self.h, ip, m, off.ctypes.data_as(P),
+                                            nbr.ctypes.data_as(P), int(nbr.size)))
+        return off, nbr[: int(off[-1])]
+
+    def rebuild(self):
+        _check(self.h, load().bbmd_rebuild(self.h))
+
+    def info(self):
+        i = bbmd_info()
+        _check(self.h, load().bbmd_get_info(self.h, C.byref(i)))
+        return {"n": i.n, "fix_exponent": i.fix_exponent, "nc": list(i.nc),
+                "cell_side_fix": list(i.cell_side_fix), "list_capacity": i.list_capacity,
+                "stencil_capacity": i.stencil_capacity, "device_bytes": i.device_bytes}

@@ -1,0 +1,816 @@
+// C ABI of libbbmd (declared in include/bbmd.h): handle life cycle, device memory plan,
+// the captured per-step CUDA graph and the synchronising queries.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bbmd_internal.cuh"
+
+using namespace bbmd;
+
+struct bbmd_sim {
+    bbmd_params P;
+    DevSim d;
+    double box[3];
+    cudaStream_t st = nullptr;
+    bbmd_alloc alloc;
+    bool have_alloc = false;
+    std::vector<std::pair<void*, size_t>> blocks;
+    int64_t bytes = 0;
+    std::string err;
+    double* dout = nullptr;          // device scratch for reduction results (64 doubles)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [thermostatted]
+    int32_t* gr_scratch = nullptr;
+    int64_t gr_scratch_n = 0;
+    unsigned long long* gr_counts = nullptr;
+    int gr_nbins = 0;
+    bool ref_set = false;
+    int sticky = 0;
+};
+
+namespace {
+
+void* dev_alloc(bbmd_sim* s, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (s->have_alloc) {
+        p = s->alloc.alloc(bytes, s->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        s->blocks.push_back({p, bytes});
+        s->bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+void dev_free(bbmd_sim* s, void* p) {
+    if (!p) return;
+    for (size_t k = 0; k < s->blocks.size(); ++k) {
+        if (s->blocks[k].first == p) {
+            s->bytes -= (int64_t)s->blocks[k].second;
+            s->blocks.erase(s->blocks.begin() + (long)k);
+            break;
+        }
+    }
+    if (s->have_alloc)
+        s->alloc.free(p, s->alloc.ctx);
+    else
+        cudaFree(p);
+}
+
+bbmd_status fail(bbmd_sim* s, bbmd_status code, const std::string& msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+bbmd_status cuda_check(bbmd_sim* s, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return BBMD_OK;
+    return fail(s, BBMD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                                      \
+    do {                                                              \
+        bbmd_status _r = cuda_check(sim, (expr), #expr);              \
+        if (_r != BBMD_OK) return _r;                                 \
+    } while (0)
+
+#define LAUNCHED(what)                                                \
+    do {                                                              \
+        bbmd_status _r = cuda_check(sim, cudaGetLastError(), what);   \
+        if (_r != BBMD_OK) return _r;                                 \
+    } while (0)
+
+int fix_exponent(const double L[3]) {
+    double m = std::fmax(L[0], std::fmax(L[1], L[2]));
+    int e;
+    std::frexp(m, &e);
+    return 61 - (e - 1);
+}
+
+int bitlen(uint64_t v) {
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+// Cell grid rule of bbmd.h.  Returns false if some axis has fewer than 3 cells.
+bool cell_grid(const double L[3], int k, double rcell, int32_t nc[3], int64_t D[3]) {
+    for (int d = 0; d < 3; ++d) {
+        int64_t Lf = std::llrint(std::ldexp(L[d], k));
+        int64_t m = (int64_t)std::floor(L[d] / rcell);
+        for (;;) {
+            if (m < 3) return false;
+            uint64_t q = (uint64_t)(Lf / m);
+            int bl = bitlen(q);
+            if (bl > 24) q &= ~((((uint64_t)1) << (bl - 24)) - 1);
+            if (std::ldexp((double)q, -k) >= rcell) {
+                nc[d] = (int32_t)m;
+                D[d] = (int64_t)q;
+                break;
+            }
+            --m;
+        }
+    }
+    return true;
+}
+
+// Untruncated pair energy and derivative of Eq. lj0 / Eq. sc0.
+void raw_pair(int pot, double eps, double sig, double r, double* V, double* dV) {
+    double sr = sig / r, sr6 = sr * sr * sr * sr * sr * sr, sr12 = sr6 * sr6;
+    if (pot == BBMD_POT_LJ) {
+        *V = 4.0 * eps * (sr12 - sr6);
+        *dV = 4.0 * eps * (-12.0 * sr12 + 6.0 * sr6) / r;
+    } else {
+        *V = 4.0 * eps * sr12;
+        *dV = -48.0 * eps * sr12 / r;
+    }
+}
+
+void fill_pair_table(const bbmd_params& P, PairTab& t) {
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            int k = a * 2 + b;
+            double rc = P.rcut[a][b], sig = P.sigma[a][b], eps = P.eps[a][b];
+            double rc2 = rc * rc;
+            double R = rc + P.skin;
+            double R2 = R * R;
+            t.rc2[k] = rc2;
+            t.R2[k] = R2;
+            t.rc2lo[k] = (float)(rc2 * (1.0 - (double)kBand));
+            t.rc2hi[k] = (float)(rc2 * (1.0 + (double)kBand));
+            t.R2lo[k] = (float)(R2 * (1.0 - (double)kBand));
+            t.R2hi[k] = (float)(R2 * (1.0 + (double)kBand));
+            t.dsig2[k] = sig * sig;
+            t.deps48[k] = 48.0 * eps;
+            t.deps4[k] = 4.0 * eps;
+            double Vc, dVc;
+            raw_pair(P.potential, eps, sig, rc, &Vc, &dVc);
+            t.dvshift[k] = P.shift == BBMD_SHIFT_NONE ? 0.0 : Vc;
+            t.dfcut[k] = P.shift == BBMD_SHIFT_FORCE ? dVc : 0.0;
+            t.drc[k] = rc;
+            t.sig2[k] = (float)t.dsig2[k];
+            t.eps48[k] = (float)t.deps48[k];
+            t.eps4[k] = (float)t.deps4[k];
+            t.vshift[k] = (float)t.dvshift[k];
+            t.fcut[k] = (float)t.dfcut[k];
+        }
+    for (int a = 0; a < 2; ++a) {
+        t.mass[a] = (float)P.mass[a];
+        t.dmass[a] = P.mass[a];
+    }
+    t.potential = P.potential;
+    t.shift = P.shift;
+}
+
+bbmd_status validate(const bbmd_params* P, int64_t n, const double* box, std::string& msg) {
+    if (!P || !box) return msg = "params and box are required", BBMD_ERR_ARG;
+    if (n < 2 || n > 2000000000LL) return msg = "n must be in [2, 2e9]", BBMD_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(box[d] >= 1.0 && box[d] < 1e9)) return msg = "box sides must be in [1, 1e9)", BBMD_ERR_ARG;
+    if (P->potential != BBMD_POT_LJ && P->potential != BBMD_POT_SOFT) return msg = "potential", BBMD_ERR_ARG;
+    if (P->shift < 0 || P->shift > 2) return msg = "shift", BBMD_ERR_ARG;
+    if (P->precision != BBMD_PREC_MIXED && P->precision != BBMD_PREC_FP64) return msg = "precision", BBMD_ERR_ARG;
+    if (P->nbr_mode != BBMD_NBR_VERLET && P->nbr_mode != BBMD_NBR_CELL) return msg = "nbr_mode", BBMD_ERR_ARG;
+    if (!(P->skin >= 0.0 && P->skin < 10.0)) return msg = "skin", BBMD_ERR_ARG;
+    for (int a = 0; a < 2; ++a) {
+        if (!(P->mass[a] > 0.0)) return msg = "mass must be > 0", BBMD_ERR_ARG;
+        for (int b = 0; b < 2; ++b) {
+            if (!(P->rcut[a][b] > 0.0) || !(P->sigma[a][b] > 0.0) || !(P->eps[a][b] >= 0.0))
+                return msg = "rcut, sigma > 0 and eps >= 0 required", BBMD_ERR_ARG;
+            if (P->rcut[a][b] != P->rcut[b][a] || P->sigma[a][b] != P->sigma[b][a] ||
+                P->eps[a][b] != P->eps[b][a])
+                return msg = "pair tables must be symmetric", BBMD_ERR_ARG;
+        }
+    }
+    if (P->list_capacity < 0 || P->list_capacity > 4096) return msg = "list_capacity", BBMD_ERR_ARG;
+    if (P->stencil_capacity < 0 || P->stencil_capacity > 8192) return msg = "stencil_capacity", BBMD_ERR_ARG;
+    return BBMD_OK;
+}
+
+bool all_finite(const double* a, int64_t m) {
+    if (!a) return true;
+    for (int64_t i = 0; i < m; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+bbmd_status read_status(bbmd_sim* sim) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, &sim->d.sc->status, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+    CK(cudaStreamSynchronize(sim->st));
+    sim->sticky |= st;
+    if (sim->sticky & (ST_LIST_OVERFLOW | ST_STENCIL_OVERFLOW))
+        return fail(sim, BBMD_ERR_LIST_OVERFLOW,
+                    "a Verlet list or staged stencil exceeded its capacity (raise list_capacity / "
+                    "stencil_capacity)");
+    if (sim->sticky & (ST_NONFINITE | ST_VEL_RANGE))
+        return fail(sim, BBMD_ERR_NUMERIC, "non-finite force or velocity beyond the fixed-point range");
+    if (sim->sticky & ST_TIMEOUT) return fail(sim, BBMD_ERR_TIMEOUT, "a bounded device wait gave up");
+    return BBMD_OK;
+}
+
+void enqueue_rebuild(bbmd_sim* sim) {
+    launch_rebuild_chain(sim->d, sim->st);
+    launch_list_build(sim->d, sim->st);
+}
+
+// Force a rebuild now: set the flag, run the chain and clear it.
+bbmd_status rebuild_now(bbmd_sim* sim) {
+    int one = 1;
+    CK(cudaMemcpyAsync(&sim->d.sc->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+    enqueue_rebuild(sim);
+    launch_clear_rebuild(sim->d, sim->st);
+    LAUNCHED("rebuild");
+    return BBMD_OK;
+}
+
+bbmd_status refresh_forces_and_K(bbmd_sim* sim) {
+    launch_force(sim->d, sim->st, false, false);
+    launch_state_sums(sim->d, sim->st);
+    launch_reduce_partials(sim->d, sim->st, 4, sim->dout);
+    LAUNCHED("forces");
+    // sc->K <- KE of the stored velocities
+    CK(cudaMemcpyAsync(&sim->d.sc->K, sim->dout, sizeof(double), cudaMemcpyDeviceToDevice, sim->st));
+    return BBMD_OK;
+}
+
+void free_graphs(bbmd_sim* sim) {
+    for (auto& g : sim->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+bbmd_status build_graph(bbmd_sim* sim, int nh) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(sim->st, cudaStreamCaptureModeThreadLocal));
+    launch_integrate(sim->d, sim->st);
+    enqueue_rebuild(sim);
+    launch_force(sim->d, sim->st, false, nh != 0);
+    launch_finalize(sim->d, sim->st, nh != 0);
+    cudaError_t e = cudaStreamEndCapture(sim->st, &g);
+    CK(e);
+    e = cudaGraphInstantiate(&sim->graph[nh], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return BBMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3],
+                        const uint8_t* species, const double* pos, const double* vel, double T0,
+                        uint64_t seed, void* stream, const bbmd_alloc* alloc, bbmd_sim** out) {
+    if (!out) return BBMD_ERR_ARG;
+    *out = nullptr;
+    std::string msg;
+    bbmd_status vs = validate(params, n, box, msg);
+    if (vs != BBMD_OK) {
+        std::fprintf(stderr, "bbmd_create: %s\n", msg.c_str());
+        return vs;
+    }
+    if (!species) return BBMD_ERR_ARG;
+    if (!(T0 >= 0.0)) return BBMD_ERR_ARG;
+    if (!all_finite(pos, 3 * n) || !all_finite(vel, 3 * n)) {
+        std::fprintf(stderr, "bbmd_create: non-finite positions or velocities\n");
+        return BBMD_ERR_ARG;
+    }
+    int m_fcc = 0;
+    if (!pos) {
+        m_fcc = (int)std::llround(std::cbrt((double)n / 4.0));
+        if (4LL * m_fcc * m_fcc * m_fcc != n) return BBMD_ERR_ARG;
+    }
+    bbmd_sim* sim = new bbmd_sim();
+    sim->P = *params;
+    sim->st = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+        sim->alloc = *alloc;
+        sim->have_alloc = true;
+    }
+    for (int d = 0; d < 3; ++d) sim->box[d] = box[d];
+    DevSim& D = sim->d;
+    std::memset(&D, 0, sizeof(D));
+    D.n = n;
+    D.npad = (n + 63) / 64 * 64;
+    D.kexp = fix_exponent(box);
+    D.sx = std::ldexp(1.0f, -D.kexp);
+    D.sxd = std::ldexp(1.0, -D.kexp);
+    for (int d = 0; d < 3; ++d) D.Lfix[d] = std::llrint(std::ldexp(box[d], D.kexp));
+    double rcmax = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) rcmax = std::fmax(rcmax, params->rcut[a][b]);
+    double rcell = rcmax + params->skin;
+    if (!cell_grid(box, D.kexp, rcell, D.nc, D.D)) {
+        delete sim;
+        return BBMD_ERR_BOX_TOO_SMALL;
+    }
+    int64_t ncell = (int64_t)D.nc[0] * D.nc[1] * D.nc[2];
+    if (ncell > 0x7fffffffLL / 2) {
+        delete sim;
+        return BBMD_ERR_ARG;
+    }
+    D.ncell = (int32_t)ncell;
+    D.nbr_mode = params->nbr_mode;
+    D.precision = params->precision;
+    fill_pair_table(*params, D.pt);
+    double half = 0.5 * params->skin;
+    D.disp2 = (float)(half * half * (1.0 - 1e-4));
+    int lcap = params->list_capacity > 0 ? params->list_capacity : 160;
+    D.lcap8 = (lcap + 7) / 8;
+    double V = box[0] * box[1] * box[2];
+    double cellvol = std::ldexp((double)D.D[0], -D.kexp) * std::ldexp((double)D.D[1], -D.kexp) *
+                     std::ldexp((double)D.D[2], -D.kexp);
+    double mean = (double)n / V * cellvol;
+    int smax = params->stencil_capacity > 0 ? params->stencil_capacity
+                                            : (int)(27.0 * mean * 1.3 + 96.0);
+    smax = (smax + 31) / 32 * 32;
+    int smax_cap = params->precision == BBMD_PREC_FP64 ? 1500 : 3000;
+    if (smax > smax_cap) smax = smax_cap;
+    D.smax = smax;
+    {
+        size_t stencil_bytes = (size_t)kWarpsPerBlock * (smax + 1) *
+                               (params->precision == BBMD_PREC_FP64 ? 32 : 16);
+        size_t build_bytes = (size_t)kWarpsPerBlock * (smax + 1) * 16 +
+                             (size_t)kWarpsPerBlock * 32 * (D.lcap8 * 8 + 2) * 2;
+        if (stencil_bytes > 220 * 1024 ||
+            (params->nbr_mode == BBMD_NBR_VERLET && build_bytes > 220 * 1024)) {
+            std::fprintf(stderr, "bbmd_create: list/stencil capacity exceeds shared memory\n");
+            delete sim;
+            return BBMD_ERR_ARG;
+        }
+    }
+
+    prepare_force_kernels();
+    // device properties and grids
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+    D.grid_part = nsm * 8;
+    {
+        size_t per_warp = (size_t)(smax + 1) * (params->precision == BBMD_PREC_FP64 ? 32 : 16);
+        size_t blk = per_warp * kWarpsPerBlock + 1024;
+        int per_sm = (int)(220000 / blk);
+        if (per_sm < 1) per_sm = 1;
+        if (per_sm > 8) per_sm = 8;
+        D.grid_cell = nsm * per_sm;
+        if (D.grid_cell > kMaxPartials) D.grid_cell = kMaxPartials;
+    }
+
+    // memory plan
+    const int64_t np = D.npad;
+    bool ok = true;
+    auto A = [&](size_t bytes) -> void* {
+        void* p = dev_alloc(sim, bytes);
+        if (!p) ok = false;
+        return p;
+    };
+    D.x = (uint64_t*)A(3 * np * 8);
+    D.v = (int64_t*)A(3 * np * 8);
+    D.img = (int32_t*)A(3 * np * 4);
+    D.id = (int32_t*)A(np * 4);
+    D.sp = (uint8_t*)A(np);
+    D.x2 = (uint64_t*)A(3 * np * 8);
+    D.v2 = (int64_t*)A(3 * np * 8);
+    D.img2 = (int32_t*)A(3 * np * 4);
+    D.id2 = (int32_t*)A(np * 4);
+    D.sp2 = (uint8_t*)A(np);
+    D.rel = (float4*)A(np * 16);
+    D.relb = (float4*)A(np * 16);
+    D.F = (float4*)A(np * 16);
+    if (params->precision == BBMD_PREC_FP64) D.Fd = (double*)A(3 * np * 8);
+    D.ud = (double*)A(np * 8);
+    D.key = (int32_t*)A(np * 4);
+    D.perm = (int32_t*)A(np * 4);
+    D.perm_tmp = (int32_t*)A(np * 4);
+    D.count = (int32_t*)A((ncell + 1) * 4);
+    D.cursor = (int32_t*)A((ncell + 1) * 4);
+    D.cell_start = (int32_t*)A((ncell + 1) * 4);
+    D.scan_part = (int32_t*)A(((ncell + 8191) / 8192 + 1) * 4);
+    if (params->nbr_mode == BBMD_NBR_VERLET) D.list = (uint16_t*)A((size_t)D.lcap8 * np * 16);
+    D.cellmax = (uint16_t*)A(np * 2);
+    D.partials = (double*)A((size_t)8 * kMaxPartials * 8);
+    D.sc = (DevScalars*)A(sizeof(DevScalars));
+    sim->dout = (double*)A(64 * 8);
+    if (!ok) {
+        bbmd_destroy(sim);
+        return BBMD_ERR_OOM;
+    }
+    if (cudaMemsetAsync(D.sc, 0, sizeof(DevScalars), sim->st) != cudaSuccess ||
+        cudaMemsetAsync(D.cellmax, 0, np * 2, sim->st) != cudaSuccess ||
+        cudaMemsetAsync(D.img, 0, 3 * np * 4, sim->st) != cudaSuccess) {
+        bbmd_destroy(sim);
+        return BBMD_ERR_CUDA;
+    }
+
+    // initial state (id order), through temporary device buffers
+    bbmd_status rc = BBMD_OK;
+    double* tpos = nullptr;
+    double* tvel = nullptr;
+    if (cudaMemcpyAsync(D.sp2, species, (size_t)n, cudaMemcpyHostToDevice, sim->st) != cudaSuccess)
+        rc = BBMD_ERR_CUDA;
+    if (rc == BBMD_OK && pos) {
+        tpos = (double*)dev_alloc(sim, 3 * n * 8);
+        if (!tpos) rc = BBMD_ERR_OOM;
+        else if (cudaMemcpyAsync(tpos, pos, 3 * n * 8, cudaMemcpyHostToDevice, sim->st) != cudaSuccess)
+            rc = BBMD_ERR_CUDA;
+    }
+    if (rc == BBMD_OK && vel) {
+        tvel = (double*)dev_alloc(sim, 3 * n * 8);
+        if (!tvel) rc = BBMD_ERR_OOM;
+        else if (cudaMemcpyAsync(tvel, vel, 3 * n * 8, cudaMemcpyHostToDevice, sim->st) != cudaSuccess)
+            rc = BBMD_ERR_CUDA;
+    }
+    if (rc == BBMD_OK) {
+        launch_pack_state(D, sim->st, tpos, tvel, nullptr, false);
+        if (!pos) launch_init_fcc(D, sim->st, m_fcc);
+        if (!vel) {
+            double* tmp = (double*)dev_alloc(sim, (3 * n + 16) * 8);
+            if (!tmp) rc = BBMD_ERR_OOM;
+            else {
+                launch_init_mb(D, sim->st, T0, seed, tmp);
+                cudaStreamSynchronize(sim->st);
+                dev_free(sim, tmp);
+            }
+        }
+    }
+    if (rc == BBMD_OK && cudaStreamSynchronize(sim->st) != cudaSuccess) rc = BBMD_ERR_CUDA;
+    dev_free(sim, tpos);
+    dev_free(sim, tvel);
+    if (rc == BBMD_OK) rc = rebuild_now(sim);
+    if (rc == BBMD_OK) rc = refresh_forces_and_K(sim);
+    if (rc == BBMD_OK) rc = read_status(sim);
+    if (rc != BBMD_OK) {
+        std::fprintf(stderr, "bbmd_create: %s\n", sim->err.c_str());
+        bbmd_destroy(sim);
+        return rc;
+    }
+    *out = sim;
+    return BBMD_OK;
+}
+
+void bbmd_destroy(bbmd_sim* sim) {
+    if (!sim) return;
+    if (sim->st) cudaStreamSynchronize(sim->st);
+    else cudaDeviceSynchronize();
+    free_graphs(sim);
+    while (!sim->blocks.empty()) dev_free(sim, sim->blocks.back().first);
+    delete sim;
+}
+
+bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* th) {
+    if (!sim) return BBMD_ERR_ARG;
+    if (nsteps < 0 || nsteps > 0x7fffffff || !(dt > 0.0) || !(dt < 1.0))
+        return fail(sim, BBMD_ERR_ARG, "nsteps in [0, 2^31) and dt in (0, 1) required");
+    int nh = 0;
+    if (th) {
+        if (th->kind == BBMD_THERMO_NH) {
+            if (!(th->T_start > 0.0 && th->T_end > 0.0 && th->tau > 0.0))
+                return fail(sim, BBMD_ERR_ARG, "Nose-Hoover needs T_start, T_end, tau > 0");
+            nh = 1;
+        } else if (th->kind != BBMD_THERMO_NVE) {
+            return fail(sim, BBMD_ERR_ARG, "thermostat kind");
+        }
+    }
+    if (nsteps == 0) return BBMD_OK;
+    if (!sim->graph[nh]) {
+        bbmd_status r = build_graph(sim, nh);
+        if (r != BBMD_OK) return r;
+    }
+    launch_begin(sim->d, sim->st, nsteps, dt, nh ? th : nullptr);
+    LAUNCHED("begin");
+    for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(sim->graph[nh], sim->st));
+    launch_finish(sim->d, sim->st);
+    LAUNCHED("finish");
+    return BBMD_OK;
+}
+
+bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args, bbmd_obs* out) {
+    if (!sim || !out) return BBMD_ERR_ARG;
+    int nbins = args && args->nbins > 0 ? args->nbins : 500;
+    double rmax = args && args->rmax > 0.0 ? args->rmax : 5.0;
+    double kv = args && args->k > 0.0 ? args->k : 7.25;
+    if (nbins > 4096) return fail(sim, BBMD_ERR_ARG, "nbins <= 4096");
+    DevSim& D = sim->d;
+    // kinetic energy and momentum
+    launch_state_sums(D, sim->st);
+    launch_reduce_partials(D, sim->st, 4, sim->dout);
+    if (mask & (BBMD_OBS_ENERGY | BBMD_OBS_VIRIAL)) {
+        launch_force(D, sim->st, true, false);
+        launch_reduce_partials(D, sim->st, -3, sim->dout + 8);
+    }
+    if (mask & BBMD_OBS_SET_REF) {
+        if (!D.ref) {
+            D.ref = (double*)dev_alloc(sim, 3 * D.n * 8);
+            if (!D.ref) return fail(sim, BBMD_ERR_OOM, "reference positions");
+            free_graphs(sim);  // the captured kernels hold the old DevSim copy
+        }
+        launch_set_ref(D, sim->st);
+        sim->ref_set = true;
+    }
+    if (mask & (BBMD_OBS_MSD | BBMD_OBS_FS)) {
+        if (!sim->ref_set) return fail(sim, BBMD_ERR_STATE, "MSD/FS need SET_REF first");
+        launch_msd_fs(D, sim->st, kv, sim->dout + 16);
+    }
+    std::vector<unsigned long long> counts;
+    if (mask & BBMD_OBS_GR) {
+        if (!sim->gr_counts || sim->gr_nbins < nbins) {
+            dev_free(sim, sim->gr_counts);
+            sim->gr_counts = (unsigned long long*)dev_alloc(sim, (size_t)4 * nbins * 8);
+            sim->gr_nbins = nbins;
+        }
+        int64_t ncg = 1;
+        for (int d = 0; d < 3; ++d) {
+            int m = (int)std::floor(sim->box[d] / rmax);
+            ncg *= m < 1 ? 1 : m;
+        }
+        int64_t need = 2 * D.n + 3 * (ncg + 1);
+        if (sim->gr_scratch_n < need) {
+            dev_free(sim, sim->gr_scratch);
+            sim->gr_scratch = (int32_t*)dev_alloc(sim, (size_t)need * 4);
+            sim->gr_scratch_n = sim->gr_scratch ? need : 0;
+        }
+        if (!sim->gr_counts || !sim->gr_scratch) return fail(sim, BBMD_ERR_OOM, "g(r) scratch");
+        if (launch_gr(D, sim->st, nbins, rmax, sim->gr_counts, sim->gr_scratch, nullptr,
+                      sim->gr_scratch_n) != 0)
+            return fail(sim, BBMD_ERR_STATE, "g(r) scratch too small");
+        counts.resize((size_t)4 * nbins);
+        CK(cudaMemcpyAsync(counts.data(), sim->gr_counts, counts.size() * 8, cudaMemcpyDeviceToHost,
+                           sim->st));
+    }
+    LAUNCHED("observe");
+    double h[32];
+    DevScalars scl;
+    CK(cudaMemcpyAsync(h, sim->dout, sizeof(h), cudaMemcpyDeviceToHost, sim->st));
+    CK(cudaMemcpyAsync(&scl, D.sc, sizeof(scl), cudaMemcpyDeviceToHost, sim->st));
+    CK(cudaStreamSynchronize(sim->st));
+    bbmd_status rs = read_status(sim);
+    if (rs != BBMD_OK) return rs;
+    double Vol = sim->box[0] * sim->box[1] * sim->box[2];
+    double g = (double)(3 * D.n - 3);
+    out->ke = h[0];
+    out->momentum[0] = h[1];
+    out->momentum[1] = h[2];
+    out->momentum[2] = h[3];
+    out->temperature = 2.0 * h[0] / g;
+    out->step = scl.step;
+    out->n_rebuilds = scl.n_rebuilds;
+    out->xi = scl.xi;
+    out->eta = scl.eta;
+    if (mask & (BBMD_OBS_ENERGY | BBMD_OBS_VIRIAL)) {
+        out->pe = h[9];
+        out->virial = h[10];
+        out->pressure = (2.0 * h[0] + h[10]) / (3.0 * Vol);
+        double E = h[0] + h[9];
+        if (scl.kind == BBMD_THERMO_NH && scl.tau > 0.0 && scl.T_last > 0.0) {
+            double Q = g * scl.T_last * scl.tau * scl.tau;
+            E += 0.5 * Q * scl.xi * scl.xi + g * scl.T_last * scl.eta;
+        }
+        out->conserved = E;
+    }
+    if (mask & (BBMD_OBS_MSD | BBMD_OBS_FS)) {
+        for (int a = 0; a < 2; ++a) {
+            double cnt = h[16 + 4 + a];
+            out->msd[a] = cnt > 0 ? h[16 + a] / cnt : 0.0;
+            out->fs[a] = cnt > 0 ? h[16 + 2 + a] / cnt : 0.0;
+        }
+    }
+    if (mask & BBMD_OBS_GR) {
+        double Ns[2] = {0.0, 0.0};
+        // species counts from the pair totals are not exact for empty shells; count directly
+        std::vector<uint8_t> spc((size_t)D.n);
+        CK(cudaMemcpy(spc.data(), D.sp, (size_t)D.n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < D.n; ++i) Ns[spc[(size_t)i]] += 1.0;
+        double dr = rmax / (double)nbins;
+        const double pi = 3.14159265358979323846;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                double nb = Ns[b] - (a == b ? 1.0 : 0.0);
+                for (int q = 0; q < nbins; ++q) {
+                    size_t k = (size_t)(a * 2 + b) * nbins + q;
+                    if (out->gr_counts) out->gr_counts[k] = counts[k];
+                    if (out->gr) {
+                        double r0 = dr * (double)q, r1 = dr * (double)(q + 1);
+                        double shell = (4.0 * pi / 3.0) * (r1 * r1 * r1 - r0 * r0 * r0);
+                        double den = Ns[a] * nb * shell;
+                        out->gr[k] = den > 0.0 ? Vol * (double)counts[k] / den : 0.0;
+                    }
+                }
+            }
+    }
+    return BBMD_OK;
+}
+
+bbmd_status bbmd_minimize(bbmd_sim* sim, int64_t nsteps, double hmax, double dmax) {
+    if (!sim || nsteps < 0 || !(hmax > 0.0) || !(dmax > 0.0)) return BBMD_ERR_ARG;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        launch_force(sim->d, sim->st, false, false);
+        launch_sd_step(sim->d, sim->st, hmax, dmax);
+        enqueue_rebuild(sim);
+        launch_clear_rebuild(sim->d, sim->st);
+    }
+    LAUNCHED("minimize");
+    launch_force(sim->d, sim->st, false, false);
+    LAUNCHED("minimize forces");
+    return read_status(sim);
+}
+
+bbmd_status bbmd_get_state(bbmd_sim* sim, double* pos, double* vel, int32_t* image) {
+    if (!sim) return BBMD_ERR_ARG;
+    const int64_t n = sim->d.n;
+    double* tp = pos ? (double*)dev_alloc(sim, 3 * n * 8) : nullptr;
+    double* tv = vel ? (double*)dev_alloc(sim, 3 * n * 8) : nullptr;
+    int32_t* ti = image ? (int32_t*)dev_alloc(sim, 3 * n * 4) : nullptr;
+    bbmd_status rc = BBMD_OK;
+    if ((pos && !tp) || (vel && !tv) || (image && !ti)) rc = fail(sim, BBMD_ERR_OOM, "get_state");
+    if (rc == BBMD_OK) {
+        launch_unpack_state(sim->d, sim->st, tp, tv, ti);
+        rc = cuda_check(sim, cudaGetLastError(), "unpack");
+    }
+    if (rc == BBMD_OK && pos)
+        rc = cuda_check(sim, cudaMemcpyAsync(pos, tp, 3 * n * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK && vel)
+        rc = cuda_check(sim, cudaMemcpyAsync(vel, tv, 3 * n * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK && image)
+        rc = cuda_check(sim, cudaMemcpyAsync(image, ti, 3 * n * 4, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+    dev_free(sim, tp);
+    dev_free(sim, tv);
+    dev_free(sim, ti);
+    if (rc != BBMD_OK) return rc;
+    return read_status(sim);
+}
+
+bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
+                           const int32_t* image) {
+    if (!sim || !pos || !vel) return BBMD_ERR_ARG;
+    const int64_t n = sim->d.n;
+    if (!all_finite(pos, 3 * n) || !all_finite(vel, 3 * n))
+        return fail(sim, BBMD_ERR_ARG, "non-finite positions or velocities");
+    double* tp = (double*)dev_alloc(sim, 3 * n * 8);
+    double* tv = (double*)dev_alloc(sim, 3 * n * 8);
+    int32_t* ti = image ? (int32_t*)dev_alloc(sim, 3 * n * 4) : nullptr;
+    bbmd_status rc = BBMD_OK;
+    if (!tp || !tv || (image && !ti)) rc = fail(sim, BBMD_ERR_OOM, "set_state");
+    if (rc == BBMD_OK)
+        rc = cuda_check(sim, cudaMemcpyAsync(tp, pos, 3 * n * 8, cudaMemcpyHostToDevice, sim->st), "H2D");
+    if (rc == BBMD_OK)
+        rc = cuda_check(sim, cudaMemcpyAsync(tv, vel, 3 * n * 8, cudaMemcpyHostToDevice, sim->st), "H2D");
+    if (rc == BBMD_OK && image)
+        rc = cuda_check(sim, cudaMemcpyAsync(ti, image, 3 * n * 4, cudaMemcpyHostToDevice, sim->st), "H2D");
+    if (rc == BBMD_OK) {
+        launch_pack_state(sim->d, sim->st, tp, tv, ti, true);
+        rc = cuda_check(sim, cudaGetLastError(), "pack");
+    }
+    if (rc == BBMD_OK) rc = rebuild_now(sim);
+    if (rc == BBMD_OK) rc = refresh_forces_and_K(sim);
+    if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+    dev_free(sim, tp);
+    dev_free(sim, tv);
+    dev_free(sim, ti);
+    if (rc != BBMD_OK) return rc;
+    return read_status(sim);
+}
+
+bbmd_status bbmd_get_forces(bbmd_sim* sim, double* F, double* u) {
+    if (!sim || !F) return BBMD_ERR_ARG;
+    const int64_t n = sim->d.n;
+    launch_force(sim->d, sim->st, u != nullptr, false);
+    double* tf = (double*)dev_alloc(sim, 3 * n * 8);
+    double* tu = u ? (double*)dev_alloc(sim, n * 8) : nullptr;
+    bbmd_status rc = BBMD_OK;
+    if (!tf || (u && !tu)) rc = fail(sim, BBMD_ERR_OOM, "get_forces");
+    if (rc == BBMD_OK) {
+        launch_unpack_forces(sim->d, sim->st, tf, tu);
+        rc = cuda_check(sim, cudaGetLastError(), "unpack forces");
+    }
+    if (rc == BBMD_OK)
+        rc = cuda_check(sim, cudaMemcpyAsync(F, tf, 3 * n * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK && u)
+        rc = cuda_check(sim, cudaMemcpyAsync(u, tu, n * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+    dev_free(sim, tf);
+    dev_free(sim, tu);
+    if (rc != BBMD_OK) return rc;
+    return read_status(sim);
+}
+
+bbmd_status bbmd_get_cells(bbmd_sim* sim, int64_t* cell) {
+    if (!sim || !cell) return BBMD_ERR_ARG;
+    const int64_t n = sim->d.n;
+    int64_t* tc = (int64_t*)dev_alloc(sim, n * 8);
+    if (!tc) return fail(sim, BBMD_ERR_OOM, "get_cells");
+    launch_unpack_cells(sim->d, sim->st, tc);
+    bbmd_status rc = cuda_check(sim, cudaGetLastError(), "unpack cells");
+    if (rc == BBMD_OK)
+        rc = cuda_check(sim, cudaMemcpyAsync(cell, tc, n * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+    dev_free(sim, tc);
+    return rc;
+}
+
+bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int64_t* offsets,
+                               int64_t* nbr, int64_t cap) {
+    if (!sim || !offsets) return BBMD_ERR_ARG;
+    if (sim->d.nbr_mode != BBMD_NBR_VERLET) return fail(sim, BBMD_ERR_STATE, "no stored list in cell mode");
+    const int64_t n = sim->d.n;
+    if (!ids) m = n;
+    if (m < 0 || m > n) return fail(sim, BBMD_ERR_ARG, "m");
+    int32_t* sel = nullptr;
+    if (ids) {
+        std::vector<int32_t> slot((size_t)n);
+        for (int64_t t = 0; t < m; ++t)
+            if (ids[t] < 0 || ids[t] >= n) return fail(sim, BBMD_ERR_ARG, "id out of range");
+        int32_t* slot_of = (int32_t*)dev_alloc(sim, n * 4);
+        sel = (int32_t*)dev_alloc(sim, (m + 1) * 4);
+        if (!slot_of || !sel) {
+            dev_free(sim, slot_of);
+            dev_free(sim, sel);
+            return fail(sim, BBMD_ERR_OOM, "get_neighbors");
+        }
+        launch_slot_of(sim->d, sim->st, slot_of);
+        CK(cudaMemcpyAsync(slot.data(), slot_of, n * 4, cudaMemcpyDeviceToHost, sim->st));
+        CK(cudaStreamSynchronize(sim->st));
+        std::vector<int32_t> hs((size_t)m + 1);
+        for (int64_t t = 0; t < m; ++t) hs[(size_t)t] = slot[(size_t)ids[t]];
+        CK(cudaMemcpyAsync(sel, hs.data(), m * 4, cudaMemcpyHostToDevice, sim->st));
+        CK(cudaStreamSynchronize(sim->st));
+        dev_free(sim, slot_of);
+    }
+    int64_t* tcnt = (int64_t*)dev_alloc(sim, (m + 1) * 8);
+    if (!tcnt) {
+        dev_free(sim, sel);
+        return fail(sim, BBMD_ERR_OOM, "get_neighbors");
+    }
+    launch_list_counts(sim->d, sim->st, sel, m, tcnt);
+    std::vector<int64_t> cnt((size_t)m + 1);
+    bbmd_status rc = cuda_check(sim, cudaGetLastError(), "list counts");
+    if (rc == BBMD_OK && m > 0)
+        rc = cuda_check(sim, cudaMemcpyAsync(cnt.data(), tcnt, m * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+    if (rc == BBMD_OK) {
+        offsets[0] = 0;
+        for (int64_t t = 0; t < m; ++t) offsets[t + 1] = offsets[t] + cnt[(size_t)t];
+    }
+    if (rc == BBMD_OK && nbr) {
+        if (cap < offsets[m]) {
+            rc = fail(sim, BBMD_ERR_ARG, "neighbour buffer too small");
+        } else {
+            int64_t* tnb = (int64_t*)dev_alloc(sim, (offsets[m] + 1) * 8);
+            if (!tnb) rc = fail(sim, BBMD_ERR_OOM, "get_neighbors");
+            if (rc == BBMD_OK && m > 0)
+                rc = cuda_check(sim, cudaMemcpyAsync(tcnt, offsets, m * 8, cudaMemcpyHostToDevice, sim->st), "H2D");
+            if (rc == BBMD_OK) {
+                launch_list_ids(sim->d, sim->st, sel, m, tcnt, tnb);
+                rc = cuda_check(sim, cudaGetLastError(), "list ids");
+            }
+            if (rc == BBMD_OK && offsets[m] > 0)
+                rc = cuda_check(sim, cudaMemcpyAsync(nbr, tnb, offsets[m] * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+            if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+            dev_free(sim, tnb);
+        }
+    }
+    dev_free(sim, tcnt);
+    dev_free(sim, sel);
+    if (rc != BBMD_OK) return rc;
+    return read_status(sim);
+}
+
+bbmd_status bbmd_rebuild(bbmd_sim* sim) {
+    if (!sim) return BBMD_ERR_ARG;
+    bbmd_status rc = rebuild_now(sim);
+    if (rc != BBMD_OK) return rc;
+    launch_force(sim->d, sim->st, false, false);
+    LAUNCHED("rebuild forces");
+    return read_status(sim);
+}
+
+bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info) {
+    if (!sim || !info) return BBMD_ERR_ARG;
+    info->n = sim->d.n;
+    info->fix_exponent = sim->d.kexp;
+    for (int d = 0; d < 3; ++d) {
+        info->nc[d] = sim->d.nc[d];
+        info->cell_side_fix[d] = sim->d.D[d];
+    }
+    info->list_capacity = sim->d.lcap8 * 8;
+    info->stencil_capacity = sim->d.smax;
+    info->device_bytes = sim->bytes;
+    return BBMD_OK;
+}
+
+const char* bbmd_last_error(const bbmd_sim* sim) { return sim ? sim->err.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// Internal definitions shared by the CUDA translation units of libbbmd (not installed).
+//
+// Data layout in device memory (sorted order = by (cell, id) after each rebuild):
+//   x[3][npad]   int64   positions in units of 2^-k (SoA per axis)
+//   v[3][npad]   int64   velocities in units of 2^-52
+//   img[3][npad] int32   box crossings
+//   id[npad]     int32   particle id;  sp[npad] uint8 species
+//   rel[npad]    float4  position relative to the frame of its build cell, w = species
+//   relb[npad]   float4  the same at the last rebuild, w = (cell << 1) | species
+//   F[npad]      float4  mixed-precision force (w = per-particle energy on energy passes)
+//   Fd[3][npad]  double  FP64-form force
+//   list[lcap8][npad][8] uint16  Verlet list: stencil offsets in the tile's staged array
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bbmd.h"
+
+namespace bbmd {
+
+constexpr int kVelExp = 52;            // velocity unit 2^-52
+constexpr int kWarpsPerBlock = 4;      // force / list kernels: one warp per cell
+constexpr int kMaxPartials = 8192;     // per-block FP64 partial sums
+constexpr float kBand = 1e-5f;         // relative band around a threshold for the FP64 re-test
+
+// status bits (sticky, OR-ed on the device)
+enum : int32_t {
+    ST_LIST_OVERFLOW = 1,
+    ST_STENCIL_OVERFLOW = 2,
+    ST_NONFINITE = 4,
+    ST_VEL_RANGE = 8,
+    ST_TIMEOUT = 16,
+};
+
+struct DevScalars {
+    double xi, eta;          // Nose-Hoover friction and its time integral
+    double K;                // kinetic energy of the stored (full-step) velocities
+    double s_next;           // velocity scale applied by the next integrate kernel
+    double s_end;            // scale applied by the finish kernel
+    double dt, T_start, T_end, tau, g;
+    double T_last;           // target temperature of the last step
+    double pe, w;            // last energy pass
+    double kin_last;         // K of the last finalize (before NH scaling)
+    double maxf;             // steepest descent: max |F|
+    long long step, n_rebuilds;
+    int step_in_call, n_in_call, kind, pending;
+    int rebuild;             // 1: the gated rebuild kernels run in this step
+    int status;              // ST_* bits
+    int pad[2];
+};
+
+struct PairTab {
+    // FP32 tables [a*2+b]
+    float rc2lo[4], rc2hi[4];     // rcut^2 (1 -/+ band)
+    float R2lo[4], R2hi[4];       // (rcut + skin)^2 (1 -/+ band)
+    float sig2[4], eps48[4], eps4[4], vshift[4], fcut[4];
+    // FP64 tables: exact decisions and the FP64 form
+    double rc2[4], R2[4], dsig2[4], deps48[4], deps4[4], dvshift[4], dfcut[4], drc[4];
+    float mass[2];
+    double dmass[2];
+    int potential, shift;
+};
+
+struct DevSim {
+    int64_t n, npad;
+    int32_t ncell, nc[3];
+    int64_t D[3], Lfix[3];
+    int32_t kexp;
+    float sx;                // 2^-k
+    double sxd;
+    int32_t lcap8, smax;
+    int32_t nbr_mode, precision;
+    float disp2;             // rebuild threshold on |x - x_build|^2 (FP32, conservative)
+    PairTab pt;
+    uint64_t* x; int64_t* v; int32_t* img; int32_t* id; uint8_t* sp;
+    uint64_t* x2; int64_t* v2; int32_t* img2; int32_t* id2; uint8_t* sp2;
+    float4 *rel, *relb, *F;
+    double* Fd;
+    double* ud;              // per-particle FP64 energy (energy passes)
+    int32_t *key, *cell_start, *count, *cursor, *perm, *perm_tmp, *scan_part;
+    uint16_t* list;
+    uint16_t* cellmax;       // per cell: list length in units of 8 entries
+    double* partials;        // [kMaxPartials][4]
+    double* ref;             // [3][n] unwrapped reference positions by id (SET_REF)
+    DevScalars* sc;
+    int32_t grid_part;       // grid of per-particle grid-stride kernels
+    int32_t grid_cell;       // grid of warp-per-cell kernels (blocks of kWarpsPerBlock warps)
+};
+
+// ---------------------------------------------------------------- conversions ----
+
+// Correctly rounded int64 -> float using 32-bit operations (no FP64 pipe).
+__device__ __forceinline__ float i64_to_f32(long long v) {
+    if (v == 0) return 0.0f;
+    unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    int lz = __clzll(a);
+    unsigned long long m = a << lz;                    // MSB at bit 63
+    unsigned int hi = (unsigned int)(m >> 32);
+    unsigned int lo = (unsigned int)m;
+    hi |= (lo != 0u);                                  // sticky bit keeps rounding exact
+    float f = __uint2float_rn(hi);                     // 32 -> 24 bits, round to nearest
+    // multiply by 2^(32 - lz) exactly (power of two built from its bit pattern)
+    int e = 127 + 32 - lz;
+    f *= __int_as_float(e << 23);
+    return v < 0 ? -f : f;
+}
+
+// Approximate int64 -> float (error about one ulp), for velocities.
+__device__ __forceinline__ float i64_to_f32_fast(long long v) {
+    int hi = (int)(v >> 32);
+    unsigned int lo = (unsigned int)v;
+    return fmaf((float)hi, 4294967296.0f, __uint2float_rn(lo));
+}
+
+// float (already scaled, |y| < 2^62) -> int64 rounded to nearest, using 32-bit converts.
+__device__ __forceinline__ long long f32_to_i64(float y) {
+    float hf = floorf(y * 2.3283064365386963e-10f);    // y / 2^32 (exact), floored
+    float lf = fmaf(-hf, 4294967296.0f, y);            // exact low part in [0, 2^32)
+    long long hi = (long long)__float2int_rn(hf);
+    unsigned long long lo = (unsigned long long)__float2uint_rn(lf);
+    return (long long)(((unsigned long long)hi << 32) + lo);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// ------------------------------------------------------------ cells and frames ----
+
+// Cell index along one axis: a = min(nc-1, x / D) by a float estimate and exact fix-up.
+__device__ __forceinline__ int cell_axis(long long x, long long D, int nc) {
+    float est = __fdividef(i64_to_f32_fast(x), i64_to_f32_fast(D));
+    int a = (int)est;
+    if (a < 0) a = 0;
+    if (a > nc - 1) a = nc - 1;
+    while (a > 0 && (long long)a * D > x) --a;
+    while (a < nc - 1 && (long long)(a + 1) * D <= x) ++a;
+    return a;
+}
+
+// Frame point of cell a along one axis (the cell's centre on the D grid).
+__device__ __forceinline__ long long frame_axis(int a, long long D) {
+    return (long long)a * D + (D >> 1);
+}
+
+// Minimum-image reduction of an integer displacement.
+__device__ __forceinline__ long long min_image(long long d, long long L) {
+    if (2 * d > L) d -= L;
+    else if (2 * d < -L) d += L;
+    return d;
+}
+
+__device__ __forceinline__ void cell_coords(int c, const int32_t* nc, int& ax, int& ay, int& az) {
+    ax = c % nc[0];
+    int t = c / nc[0];
+    ay = t % nc[1];
+    az = t / nc[1];
+}
+
+// Exact r^2 rule in FP64 (the same IEEE operations the oracle performs).
+__device__ __forceinline__ double r2_exact(const DevSim& s, int64_t i, int64_t j) {
+    double d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        long long dx = (long long)s.x[a * s.npad + j] - (long long)s.x[a * s.npad + i];
+        dx = min_image(dx, s.Lfix[a]);
+        d[a] = __dmul_rn(__ll2double_rn(dx), s.sxd);
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+__device__ __forceinline__ void set_status(const DevSim& s, int bits) {
+    atomicOr(&s.sc->status, bits);
+}
+
+// ------------------------------------------------------------ launch wrappers ----
+// (defined in the .cu files; all enqueue on `st`)
+
+// sort / rebuild chain (gated on sc->rebuild unless noted)
+void launch_rebuild_chain(const DevSim& s, cudaStream_t st);
+// one-time kernel attributes (call before any stream capture)
+void prepare_force_kernels();
+// list build (gated)
+void launch_list_build(const DevSim& s, cudaStream_t st);
+// forces.  energy: also per-particle energy and virial partials; ke: NH kinetic partials
+void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke);
+// integrator pieces
+void launch_begin(const DevSim& s, cudaStream_t st, int64_t nsteps, double dt,
+                  const bbmd_thermostat* th);
+void launch_integrate(const DevSim& s, cudaStream_t st);
+void launch_finalize(const DevSim& s, cudaStream_t st, bool ke);
+void launch_finish(const DevSim& s, cudaStream_t st);
+void launch_state_sums(const DevSim& s, cudaStream_t st);          // KE, P partials -> sc->K etc.
+void launch_reduce_partials(const DevSim& s, cudaStream_t st, int nq, double* out_dev);
+void launch_init_fcc(const DevSim& s, cudaStream_t st, int m);
+void launch_init_mb(const DevSim& s, cudaStream_t st, double T0, uint64_t seed, double* tmp3);
+void launch_sd_step(const DevSim& s, cudaStream_t st, double hmax, double dmax);
+void launch_clear_rebuild(const DevSim& s, cudaStream_t st);
+void launch_set_ref(const DevSim& s, cudaStream_t st);
+void launch_msd_fs(const DevSim& s, cudaStream_t st, double kvec, double* out_dev);
+int launch_gr(const DevSim& s, cudaStream_t st, int nbins, double rmax,
+              unsigned long long* counts_dev, int32_t* scratch_i32, float4* scratch_f4,
+              int64_t scratch_n);
+void launch_unpack_state(const DevSim& s, cudaStream_t st, double* pos, double* vel,
+                         int32_t* img);   // device buffers, id order
+void launch_pack_state(const DevSim& s, cudaStream_t st, const double* pos, const double* vel,
+                       const int32_t* img, bool species_from_current);
+void launch_unpack_forces(const DevSim& s, cudaStream_t st, double* F, double* u);
+void launch_unpack_cells(const DevSim& s, cudaStream_t st, int64_t* cell);
+// Neighbour lists by id.  sel: slots of the m requested particles (NULL = all, output
+// in id order).
+void launch_slot_of(const DevSim& s, cudaStream_t st, int32_t* slot_of);
+void launch_list_counts(const DevSim& s, cudaStream_t st, const int32_t* sel, int64_t m,
+                        int64_t* counts);
+void launch_list_ids(const DevSim& s, cudaStream_t st, const int32_t* sel, int64_t m,
+                     const int64_t* offsets, int64_t* nbr);
+
+}  // namespace bbmd

@@ -1,0 +1,244 @@
+// Cell binning and spatial reorder (Sec. 2.2: O(N) cell search over cubic cells; the
+// paper's per-cell linked lists become a counting sort into contiguous cell segments).
+//
+// Every kernel here is gated on sc->rebuild: when the integrator has not raised the flag
+// the kernels return at once, so a captured step can always contain them.  All kernels
+// use fixed grid-stride grids (a few blocks per SM) so that a skipped rebuild costs only
+// a handful of empty launches.
+//
+// Chain: zero counts -> bin (key + histogram) -> exclusive scan -> scatter -> order each
+// cell by id (canonical order: the sorted state depends only on positions and ids) ->
+// gather into the alternate buffers (+ frame-relative FP32 copies) -> copy back.
+#include "bbmd_internal.cuh"
+
+namespace bbmd {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kThreads) k_zero(DevSim s) {
+    if (!s.sc->rebuild) return;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= s.ncell;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        s.count[c] = 0;
+        s.cursor[c] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bin(DevSim s) {
+    if (!s.sc->rebuild) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int ax = cell_axis((long long)s.x[i], s.D[0], s.nc[0]);
+        int ay = cell_axis((long long)s.x[s.npad + i], s.D[1], s.nc[1]);
+        int az = cell_axis((long long)s.x[2 * s.npad + i], s.D[2], s.nc[2]);
+        int c = (az * s.nc[1] + ay) * s.nc[0] + ax;
+        s.key[i] = c;
+        atomicAdd(&s.count[c], 1);
+    }
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ int block_scan_excl(int v, int& total) {
+    __shared__ int wsum[kScanThreads / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        wsum[lane] = xi - x;
+        if (lane == (int)(blockDim.x >> 5) - 1) total = xi;
+    }
+    __syncthreads();
+    int r = wsum[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+// pass 1: per-chunk sums of count[0 .. ncell)
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(DevSim s, int nchunks) {
+    if (!s.sc->rebuild) return;
+    __shared__ int red[kScanThreads / 32];
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        int64_t base = (int64_t)ch * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+        int acc = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            int64_t c = base + k;
+            if (c < s.ncell) acc += s.count[c];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int x = threadIdx.x < (kScanThreads / 32) ? red[threadIdx.x] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (threadIdx.x == 0) s.scan_part[ch] = x;
+        }
+        __syncthreads();
+    }
+}
+
+// pass 2: exclusive scan of the chunk sums (one block)
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(DevSim s, int nchunks) {
+    if (!s.sc->rebuild) return;
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nchunks; base += kScanThreads) {
+        int idx = base + threadIdx.x;
+        int v = idx < nchunks ? s.scan_part[idx] : 0;
+        int total = 0;
+        __shared__ int tot;
+        int ex = block_scan_excl(v, tot);
+        total = tot;
+        if (idx < nchunks) s.scan_part[idx] = ex + carry;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+// pass 3: per-chunk exclusive scan plus chunk offset -> cell_start
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(DevSim s, int nchunks) {
+    if (!s.sc->rebuild) return;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        int64_t base = (int64_t)ch * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+        int vals[kScanItems];
+        int acc = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            int64_t c = base + k;
+            vals[k] = c < s.ncell ? s.count[c] : 0;
+            acc += vals[k];
+        }
+        __shared__ int tot;
+        int ex = block_scan_excl(acc, tot) + s.scan_part[ch];
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            int64_t c = base + k;
+            if (c < s.ncell) s.cell_start[c] = ex;
+            ex += vals[k];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.cell_start[s.ncell] = (int32_t)s.n;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scatter(DevSim s) {
+    if (!s.sc->rebuild) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int c = s.key[i];
+        int slot = s.cell_start[c] + atomicAdd(&s.cursor[c], 1);
+        s.perm_tmp[slot] = (int32_t)i;
+    }
+}
+
+// Order each cell's particles by id: rank = number of smaller ids in the cell.
+__global__ void __launch_bounds__(kThreads) k_cellsort(DevSim s) {
+    if (!s.sc->rebuild) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < s.ncell;
+         c += nwarps) {
+        int start = s.cell_start[c];
+        int cnt = s.cell_start[c + 1] - start;
+        if (cnt <= 32) {
+            int pe = lane < cnt ? s.perm_tmp[start + lane] : 0;
+            int ide = lane < cnt ? s.id[pe] : 0x7fffffff;
+            int rank = 0;
+            for (int f = 0; f < cnt; ++f) {
+                int other = __shfl_sync(0xffffffffu, ide, f);
+                rank += other < ide;
+            }
+            if (lane < cnt) s.perm[start + rank] = pe;
+        } else {
+            for (int e = lane; e < cnt; e += 32) {
+                int pe = s.perm_tmp[start + e];
+                int ide = s.id[pe];
+                int rank = 0;
+                for (int f = 0; f < cnt; ++f) rank += s.id[s.perm_tmp[start + f]] < ide;
+                s.perm[start + rank] = pe;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gather(DevSim s) {
+    if (!s.sc->rebuild) return;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t o = s.perm[k];
+        int c = s.key[o];
+        int ax, ay, az;
+        cell_coords(c, s.nc, ax, ay, az);
+        int a3[3] = {ax, ay, az};
+        float r[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            uint64_t xv = s.x[d * s.npad + o];
+            s.x2[d * s.npad + k] = xv;
+            s.v2[d * s.npad + k] = s.v[d * s.npad + o];
+            s.img2[d * s.npad + k] = s.img[d * s.npad + o];
+            long long rel = (long long)xv - frame_axis(a3[d], s.D[d]);
+            r[d] = i64_to_f32(rel) * s.sx;
+        }
+        s.id2[k] = s.id[o];
+        uint8_t spc = s.sp[o];
+        s.sp2[k] = spc;
+        s.relb[k] = make_float4(r[0], r[1], r[2], __int_as_float((c << 1) | spc));
+        s.rel[k] = make_float4(r[0], r[1], r[2], __int_as_float((int)spc));
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_copyback(DevSim s) {
+    if (!s.sc->rebuild) return;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            s.x[d * s.npad + k] = s.x2[d * s.npad + k];
+            s.v[d * s.npad + k] = s.v2[d * s.npad + k];
+            s.img[d * s.npad + k] = s.img2[d * s.npad + k];
+        }
+        s.id[k] = s.id2[k];
+        s.sp[k] = s.sp2[k];
+    }
+}
+
+}  // namespace
+
+void launch_rebuild_chain(const DevSim& s, cudaStream_t st) {
+    int nchunks = (int)((s.ncell + kScanChunk - 1) / kScanChunk);
+    int gscan = nchunks < 1024 ? nchunks : 1024;
+    if (gscan < 1) gscan = 1;
+    k_zero<<<s.grid_part, kThreads, 0, st>>>(s);
+    k_bin<<<s.grid_part, kThreads, 0, st>>>(s);
+    k_scan_reduce<<<gscan, kScanThreads, 0, st>>>(s, nchunks);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(s, nchunks);
+    k_scan_down<<<gscan, kScanThreads, 0, st>>>(s, nchunks);
+    k_scatter<<<s.grid_part, kThreads, 0, st>>>(s);
+    k_cellsort<<<s.grid_part, kThreads, 0, st>>>(s);
+    k_gather<<<s.grid_part, kThreads, 0, st>>>(s);
+    k_copyback<<<s.grid_part, kThreads, 0, st>>>(s);
+}
+
+}  // namespace bbmd

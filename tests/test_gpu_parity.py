@@ -1,0 +1,403 @@
+"""GPU-vs-oracle parity through the C ABI (libbbmd.so), on seeded generator inputs.
+
+Bars: cells and Verlet neighbour sets bit-exact; mixed-precision forces e_i <= 1e-5
+(median) and <= 1e-4 (max); potential energy per particle within 1e-6; 100-step position
+RMS <= 1e-4; the FP64 form within 1e-10 relative per force."""
+import numpy as np
+import pytest
+
+import oracle
+from inputs import generate as gen
+from tests.helpers import force_errors, min_image_rms, mixture, oracle_params, quantized
+
+pytestmark = pytest.mark.gpu
+
+bbmd = pytest.importorskip("paper_1105_5613_gb300.bbmd")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_5613_gb300 import build as b
+
+    b.build()
+    bbmd.load()
+
+
+def make(ncell=10, seed=0, T=2.0, shake=0.1, **kw):
+    n, L, pos, vel, sp = mixture(ncell, seed=seed, T=T, shake=shake)
+    p = bbmd.ka_params(**kw)
+    sim = bbmd.Sim(p, n, L, sp, pos, vel)
+    return sim, n, L, pos, vel, sp, p
+
+
+# ------------------------------------------------------------------- binning / lists ----
+
+@pytest.mark.parametrize("shake", [0.0, 0.12])
+def test_cells_bit_exact(shake):
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=shake)
+    info = sim.info()
+    xq, xfix, k = quantized(pos, L)
+    assert info["fix_exponent"] == k
+    nc, D = oracle.cell_grid(L, k, 2.5 + 0.3)
+    assert list(nc) == info["nc"] and list(D) == info["cell_side_fix"]
+    assert np.array_equal(sim.get_cells(), oracle.bin_cells(xfix, nc, D))
+    sim.close()
+
+
+@pytest.mark.parametrize("ncell,shake", [(10, 0.0), (10, 0.15), (7, 0.2)])
+def test_neighbor_sets_bit_exact(ncell, shake):
+    sim, n, L, pos, vel, sp, p = make(ncell=ncell, shake=shake)
+    xq, xfix, k = quantized(pos, L)
+    R2 = oracle.list_R2(oracle_params(p), 0.3)
+    off, nbr = sim.get_neighbors()
+    offo, nbro = oracle.neighbors(xfix, sp, L, k, R2, "cells", rcell=2.8)
+    assert np.array_equal(off, offo)
+    assert np.array_equal(nbr, nbro)
+    sim.close()
+
+
+# ---------------------------------------------------------------------------- forces ----
+
+@pytest.mark.parametrize("pot,shift", [(0, 1), (0, 0), (0, 2), (1, 1)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_forces_mixed(pot, shift, mode):
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.12, potential=pot, shift=shift,
+                                      nbr_mode=mode)
+    xq, _, _ = quantized(pos, L)
+    po = oracle_params(p)
+    Fo, uo, Wo, PEo = oracle.forces(xq, sp, L, po)
+    F, u = sim.get_forces(energies=True)
+    e = force_errors(F, Fo)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+    obs = sim.observe(bbmd.OBS_ENERGY | bbmd.OBS_VIRIAL)
+    assert abs(obs["pe"] - PEo) / n <= 1e-6
+    assert abs(obs["virial"] - Wo) / n <= 1e-5
+    assert np.abs(u - uo).max() <= 5e-5
+    sim.close()
+
+
+@pytest.mark.parametrize("shift", [1, 2])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_forces_fp64_form(shift, mode):
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.12, precision=bbmd.PREC_FP64, shift=shift,
+                                      nbr_mode=mode)
+    xq, _, _ = quantized(pos, L)
+    po = oracle_params(p)
+    Fo, uo, Wo, PEo = oracle.forces(xq, sp, L, po)
+    F, u = sim.get_forces(energies=True)
+    rel = np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), 1e-3)
+    assert rel.max() <= 1e-10, rel.max()
+    obs = sim.observe(bbmd.OBS_ENERGY | bbmd.OBS_VIRIAL)
+    assert abs(obs["pe"] - PEo) <= 1e-10 * abs(PEo)
+    assert np.allclose(u, uo, rtol=1e-10, atol=1e-12)
+    sim.close()
+
+
+def test_zero_net_force_and_lattice():
+    # perfect lattice, all A: every force vanishes (FP32 path: small residual)
+    ncell = 8
+    n = 4 * ncell ** 3
+    L = gen.box_for(n, 1.2)
+    pos = gen.fcc_lattice(ncell, L)
+    sp = np.zeros(n, dtype=np.uint8)
+    sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, pos, np.zeros((n, 3)))
+    F = sim.get_forces()
+    assert np.abs(F).max() < 1e-3
+    sim.close()
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.12)
+    F = sim.get_forces()
+    assert np.abs(F.sum(0)).max() <= 1e-6 * np.abs(F).sum()
+    sim.close()
+
+
+# ------------------------------------------------------------------- trajectories ----
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-4), (1, 1e-9)])
+def test_trajectory_nve_100_steps(prec, tol):
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.0, T=2.0, precision=prec)
+    xq, _, _ = quantized(pos, L)
+    st = oracle.MDState(xq, vel, sp, L, oracle_params(p))
+    oracle.md_run(st, 100, 0.005, use_cells=True)
+    sim.step(100, 0.005)
+    gp, gv, gi = sim.get_state()
+    assert min_image_rms(gp, st.pos, L) <= tol
+    assert np.sqrt(((gv - st.vel) ** 2).sum(1).mean()) <= 50 * tol
+    sim.close()
+
+
+def test_trajectory_split_calls_equal_one_call():
+    a, n, L, pos, vel, sp, p = make(ncell=8, shake=0.05)
+    b = bbmd.Sim(p, n, L, sp, pos, vel)
+    a.step(60, 0.005)
+    for _ in range(6):
+        b.step(10, 0.005)
+    pa, va, _ = a.get_state()
+    pb, vb, _ = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-4), (1, 1e-9)])
+def test_trajectory_nose_hoover_100_steps(prec, tol):
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.0, T=2.0, precision=prec)
+    xq, _, _ = quantized(pos, L)
+    st = oracle.MDState(xq, vel, sp, L, oracle_params(p))
+    th = (0.5, 0.5, 0.5)
+    oracle.md_run(st, 100, 0.005, thermo=th, use_cells=True)
+    sim.step(100, 0.005, (bbmd.THERMO_NH, *th))
+    gp, gv, _ = sim.get_state()
+    obs = sim.observe(bbmd.OBS_ENERGY)
+    assert min_image_rms(gp, st.pos, L) <= tol
+    assert obs["xi"] == pytest.approx(st.nh.xi, rel=50 * tol, abs=50 * tol)
+    sim.close()
+
+
+def test_nose_hoover_ramp_matches_oracle():
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.0, T=2.0)
+    xq, _, _ = quantized(pos, L)
+    st = oracle.MDState(xq, vel, sp, L, oracle_params(p))
+    th = (2.0, 0.4, 0.5)
+    oracle.md_run(st, 80, 0.005, thermo=th, use_cells=True)
+    sim.step(80, 0.005, (bbmd.THERMO_NH, *th))
+    gp, gv, _ = sim.get_state()
+    assert min_image_rms(gp, st.pos, L) <= 1e-4
+    K, _ = oracle.kinetic(st.vel, sp, oracle_params(p))
+    assert sim.observe(0)["ke"] == pytest.approx(K, rel=1e-4)
+    sim.close()
+
+
+def test_nve_energy_conservation():
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.05, T=2.0)
+    E = []
+    for _ in range(12):
+        sim.step(50, 0.005)
+        o = sim.observe(bbmd.OBS_ENERGY | bbmd.OBS_MOMENTUM)
+        E.append((o["ke"] + o["pe"]) / n)
+        assert np.abs(o["momentum"]).max() < 1e-3
+    E = np.array(E)
+    assert abs(E[-4:].mean() - E[2:6].mean()) < 1e-4, E
+    assert o["n_rebuilds"] > 5
+    sim.close()
+
+
+# ------------------------------------------------------------------- observables ----
+
+@pytest.mark.parametrize("ncell", [10, 11])
+def test_gr_counts_bit_exact(ncell):
+    sim, n, L, pos, vel, sp, p = make(ncell=ncell, shake=0.15)
+    xq, xfix, k = quantized(pos, L)
+    o = sim.observe(bbmd.OBS_GR, nbins=500, rmax=5.0)
+    ref = oracle.gr_counts(xfix, sp, L, k, 500, 5.0)
+    assert np.array_equal(o["gr_counts"], ref)
+    g = oracle.gr_normalize(ref, sp, L, 5.0)
+    assert np.allclose(o["gr"], g, rtol=1e-12, atol=1e-12)
+    sim.close()
+
+
+def test_msd_fs_rigid_translation():
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.1)
+    sim.observe(bbmd.OBS_SET_REF)
+    o = sim.observe(bbmd.OBS_MSD | bbmd.OBS_FS)
+    assert np.allclose(o["msd"], 0.0) and np.allclose(o["fs"], 1.0)
+    dvec = np.array([0.3, -0.7, 1.9])
+    moved = pos + dvec
+    img = np.floor(moved / L).astype(np.int32)
+    sim.set_state(moved - L * img, vel, img)
+    o = sim.observe(bbmd.OBS_MSD | bbmd.OBS_FS, k=7.25)
+    assert np.allclose(o["msd"], (dvec ** 2).sum(), rtol=1e-9)
+    assert np.allclose(o["fs"], np.cos(7.25 * dvec).mean(), rtol=1e-9, atol=1e-12)
+    sim.close()
+
+
+# ------------------------------------------------------------------ edge cases ----
+
+def test_edge_minimal_box_and_ragged_n():
+    # N = 864 (L = 8.96): three cells per axis, the smallest legal grid
+    sim, n, L, pos, vel, sp, p = make(ncell=6, shake=0.1)
+    assert sim.info()["nc"] == [3, 3, 3]
+    xq, xfix, k = quantized(pos, L)
+    Fo = oracle.forces(xq, sp, L, oracle_params(p))[0]
+    e = force_errors(sim.get_forces(), Fo)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4
+    sim.close()
+    # ragged N (not a lattice size), non-cubic box, random non-overlapping positions
+    n = 1237
+    box = np.array([9.5, 11.0, 10.3])
+    rng = np.random.default_rng(5)
+    pos = gen.rsa_positions(n, 9.5, 0.75, 21) * (box / 9.5)
+    sp = (rng.uniform(size=n) < 0.3).astype(np.uint8)
+    p = bbmd.ka_params()
+    sim = bbmd.Sim(p, n, box, sp, pos, np.zeros((n, 3)))
+    xfix, k = oracle.quantize(pos, box)
+    xq = oracle.dequantize(xfix, k)
+    Fo = oracle.forces(xq, sp, box, oracle_params(p))[0]
+    e = force_errors(sim.get_forces(), Fo)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4
+    R2 = oracle.list_R2(oracle_params(p), 0.3)
+    off, nbr = sim.get_neighbors()
+    offo, nbro = oracle.neighbors(xfix, sp, box, k, R2, "brute")
+    assert np.array_equal(off, offo) and np.array_equal(nbr, nbro)
+    sim.close()
+
+
+def test_edge_crowded_cells_and_single_species():
+    # a dense slab puts more than 32 particles into some cells (chunked tiles)
+    n = 2000
+    L = 11.5
+    rng = np.random.default_rng(9)
+    pos = gen.rsa_positions(n, L, 0.62, 33)
+    pos[:, 2] = pos[:, 2] * 0.6
+    sp = np.ones(n, dtype=np.uint8)
+    p = bbmd.ka_params(stencil_capacity=3000)
+    sim = bbmd.Sim(p, n, L, sp, pos, np.zeros((n, 3)))
+    xq, xfix, k = quantized(pos, L)
+    cells = sim.get_cells()
+    assert np.bincount(cells).max() > 32
+    Fo = oracle.forces(xq, sp, L, oracle_params(p))[0]
+    e = force_errors(sim.get_forces(), Fo)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4
+    off, nbr = sim.get_neighbors()
+    offo, nbro = oracle.neighbors(xfix, sp, L, k, oracle.list_R2(oracle_params(p), 0.3))
+    assert np.array_equal(off, offo) and np.array_equal(nbr, nbro)
+    sim.close()
+    _ = rng
+
+
+def test_errors_are_reported():
+    n, L, pos, vel, sp = mixture(5)
+    with pytest.raises(bbmd.BBMDError) as ei:  # 500 particles: fewer than 3 cells per axis
+        bbmd.Sim(bbmd.ka_params(), n, L, sp, pos, vel)
+    assert ei.value.code == 2
+    n, L, pos, vel, sp = mixture(8)
+    bad = bbmd.ka_params()
+    bad.mass[1] = 0.0
+    with pytest.raises(bbmd.BBMDError) as ei:
+        bbmd.Sim(bad, n, L, sp, pos, vel)
+    assert ei.value.code == 1
+    p2 = pos.copy()
+    p2[3, 1] = np.nan
+    with pytest.raises(bbmd.BBMDError) as ei:
+        bbmd.Sim(bbmd.ka_params(), n, L, sp, p2, vel)
+    assert ei.value.code == 1
+    with pytest.raises(bbmd.BBMDError) as ei:  # list capacity far too small
+        bbmd.Sim(bbmd.ka_params(list_capacity=16), n, L, sp, pos, vel)
+    assert ei.value.code == 5
+    sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, pos, vel)
+    with pytest.raises(bbmd.BBMDError):
+        sim.step(10, -1.0)
+    with pytest.raises(bbmd.BBMDError):
+        sim.observe(bbmd.OBS_MSD)  # no reference yet
+    sim.step(5, 0.005)
+    sim.close()
+
+
+def test_deterministic_repeat():
+    a, n, L, pos, vel, sp, p = make(ncell=8, shake=0.1)
+    b = bbmd.Sim(p, n, L, sp, pos, vel)
+    a.step(40, 0.005, (bbmd.THERMO_NH, 1.0, 1.0, 0.5))
+    b.step(40, 0.005, (bbmd.THERMO_NH, 1.0, 1.0, 0.5))
+    pa, va, ia = a.get_state()
+    pb, vb, ib = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(ia, ib)
+    a.close()
+    b.close()
+
+
+def test_state_round_trip_and_resume():
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.1)
+    sim.step(30, 0.005)
+    gp, gv, gi = sim.get_state()
+    twin = bbmd.Sim(p, n, L, sp, gp, gv)
+    twin.set_state(gp, gv, gi)
+    tp, tv, ti = twin.get_state()
+    assert np.array_equal(tp, gp) and np.array_equal(tv, gv) and np.array_equal(ti, gi)
+    sim.step(30, 0.005)
+    twin.step(30, 0.005)
+    ap, _, _ = sim.get_state()
+    bp, _, _ = twin.get_state()
+    assert min_image_rms(ap, bp, L) <= 1e-5
+    sim.close()
+    twin.close()
+
+
+def test_minimize_matches_oracle_energy():
+    n = 1500
+    L = gen.box_for(n, 1.2)
+    pos = gen.rsa_positions(n, L, 0.7, 3)
+    sp = gen.assign_species(n, 300, 3)
+    p = bbmd.ka_params()
+    sim = bbmd.Sim(p, n, L, sp, pos, np.zeros((n, 3)))
+    e0 = sim.observe(bbmd.OBS_ENERGY)["pe"]
+    sim.minimize(50)
+    e1 = sim.observe(bbmd.OBS_ENERGY)["pe"]
+    xq, _, _ = quantized(pos, L)
+    relaxed = oracle.sd_run(xq, sp, L, oracle_params(p), 50, use_cells=True)
+    eo = oracle.forces(relaxed, sp, L, oracle_params(p))[3]
+    assert e1 < e0
+    assert abs(e1 - eo) / n < 1e-4
+    sim.close()
+
+
+def test_device_generated_initial_state_matches_generator():
+    ncell = 9
+    n = 4 * ncell ** 3
+    L = gen.box_for(n, 1.2)
+    sp = gen.assign_species(n, n // 5, 4)
+    sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, None, None, T0=1.5, seed=4)
+    gp, gv, _ = sim.get_state()
+    xq, _, _ = quantized(gen.fcc_lattice(ncell, L), L)
+    assert np.array_equal(gp, xq)
+    ref = gen.maxwell_boltzmann(n, 1.5, 4, np.ones(n))
+    assert np.abs(gv - ref).max() < 1e-12
+    sim.close()
+
+
+def test_torch_allocator_and_stream():
+    torch = pytest.importorskip("torch")
+    n, L, pos, vel, sp = mixture(8, shake=0.1)
+    s = torch.cuda.Stream()
+    sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, pos, vel, stream=s.cuda_stream,
+                   use_torch_allocator=True)
+    assert sim.info()["device_bytes"] > 0
+    sim.step(20, 0.005)
+    o = sim.observe(bbmd.OBS_ENERGY)
+    assert np.isfinite(o["pe"])
+    sim.close()
+
+
+# -------------------------------------------------------------- full-size samples ----
+
+@pytest.mark.parametrize("ncell", [40, 160])
+def test_full_size_sampled(ncell):
+    """The benchmark configurations (256 000 and 16 384 000 particles), in the launch
+    configuration the benchmark uses: bins checked for every particle, neighbour sets
+    and forces for a seeded sample computed one by one by the oracle."""
+    n = 4 * ncell ** 3
+    L = gen.box_for(n, 1.2)
+    sp = gen.assign_species(n, n // 5, 0)
+    sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, None, None, T0=2.0, seed=0)
+    sim.step(20, 0.005, (bbmd.THERMO_NH, 2.0, 2.0, 0.5))
+    pos = gen.fcc_lattice(ncell, L)
+    # restart from generator positions with a seeded shake so no oracle input comes
+    # from the device trajectory
+    rng = np.random.default_rng(77)
+    pos = (pos + rng.uniform(-0.12, 0.12, pos.shape)) % L
+    vel = gen.maxwell_boltzmann(n, 2.0, 0, np.ones(n))
+    sim.set_state(pos, vel)
+    xq, xfix, k = quantized(pos, L)
+    nc, D = oracle.cell_grid(L, k, 2.8)
+    assert np.array_equal(sim.get_cells(), oracle.bin_cells(xfix, nc, D))
+    idx = np.sort(np.random.default_rng(1).choice(n, 400, replace=False))
+    F = sim.get_forces()
+    Fo, _ = oracle.forces_subset(xq, sp, L, oracle.ka_params(), idx)
+    e = force_errors(F[idx], Fo)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+    off, nbr = sim.get_neighbors(idx)
+    R2 = oracle.list_R2(oracle.ka_params(), 0.3)
+    offo, nbro = oracle.neighbors_subset(xfix, sp, L, k, R2, idx, 2.8)
+    assert np.array_equal(off, offo) and np.array_equal(nbr, nbro)
+    sim.close()

@@ -422,3 +422,19 @@ def test_two_body_systems_each_species_pair(method):
         assert PE == pytest.approx(-eps - 4 * eps * (2.5 ** -12 - 2.5 ** -6), rel=1e-13)
         assert np.abs(F).max() < 1e-11
         assert np.allclose(u, PE / 2)
+
+
+def test_subset_functions_equal_full():
+    pos, _, sp, L = liquid(ncell=6, seed=16, shake=0.2)
+    p = oracle.ka_params()
+    F, u, _, _ = oracle.forces(pos, sp, L, p)
+    idx = np.array([0, 5, 77, 400, 863])
+    Fs, us = oracle.forces_subset(pos, sp, L, p, idx)
+    assert np.allclose(Fs, F[idx], rtol=1e-12, atol=1e-12)
+    assert np.allclose(us, u[idx], rtol=1e-12, atol=1e-12)
+    xfix, k = oracle.quantize(pos, L)
+    R2 = oracle.list_R2(p, 0.3)
+    off, nbr = oracle.neighbors(xfix, sp, L, k, R2)
+    offs, nbrs = oracle.neighbors_subset(xfix, sp, L, k, R2, idx, 2.8)
+    for s, i in enumerate(idx):
+        assert np.array_equal(nbrs[offs[s]:offs[s + 1]], nbr[off[i]:off[i + 1]])

@@ -1,0 +1,377 @@
+"""Benchmark of the hot path: particle-steps/s of the binary Lennard-Jones mixture on one
+GB300, default workload = the 16,384,000-particle supercooling quench (FCC 4*160^3, 80:20,
+rho = 1.2, Nose-Hoover ramp 2.0 -> 0.4 over 1e5 steps, dt = 0.005, mixed precision,
+Verlet list with skin 0.3).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is device-timed (CUDA events on the handle's
+stream, state resident in HBM); `e2e` is the same metric through the C ABI with host
+buffers (upload of the state, the steps, energy read-back and download of the state).
+Under torchrun each rank runs its own independent replica (weak scaling; the single
+system is not decomposed across GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RAMP_STEPS = 100_000
+T_HIGH, T_LOW, TAU, DT = 2.0, 0.4, 0.5, 0.005
+NCELL_FCC = 160                      # N = 4 * 160^3 = 16,384,000
+FLOP_PER_HALF_PAIR = 25.0            # r^2, reciprocal, LJ force scalar and vector update
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT, FP32_PER_SM_CLK = 152, 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def ramp_T(step):
+    return T_HIGH + (T_LOW - T_HIGH) * min(step, RAMP_STEPS) / RAMP_STEPS
+
+
+def half_pairs_per_particle(rho=1.2, xb=0.2, rc_factor=2.5):
+    """Expected interacting pairs per particle inside r_c,ab (uniform-density estimate):
+    1/2 sum_ab x_a x_b rho (4 pi / 3) rc_ab^3."""
+    sig = ((1.0, 0.8), (0.8, 0.88))
+    x = (1.0 - xb, xb)
+    s = 0.0
+    for a in range(2):
+        for b in range(2):
+            rc = rc_factor * sig[a][b]
+            s += x[a] * x[b] * rho * 4.0 * math.pi / 3.0 * rc ** 3
+    return 0.5 * s
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_stream():
+    import torch
+
+    return torch.cuda.Stream()
+
+
+def run_ours(args):
+    import torch
+
+    from inputs import generate as gen
+    from paper_1105_5613_gb300 import bbmd
+    from paper_1105_5613_gb300 import build as b
+
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    b.build()
+    bbmd.load()
+    n = 4 * NCELL_FCC ** 3
+    L = gen.box_for(n, 1.2)
+    sp = gen.assign_species(n, n // 5, 0)
+    stream = make_stream()
+    p = bbmd.ka_params()
+    sim = bbmd.Sim(p, n, L, sp, None, None, T0=T_HIGH, seed=rank, stream=stream.cuda_stream,
+                   use_torch_allocator=True)
+    step = 0
+
+    def therm(k):
+        return (bbmd.THERMO_NH, ramp_T(step), ramp_T(step + k), TAU)
+
+    # the workload starts from an equilibrated liquid at T=2.0 (untimed; not part of the
+    # ramp), then untimed warm-up steps of the ramp (the first also captures the graph)
+    if args.equil > 0:
+        sim.step(args.equil, DT, (bbmd.THERMO_NH, T_HIGH, T_HIGH, TAU))
+    sim.step(args.warmup, DT, therm(args.warmup))
+    step += args.warmup
+    stream.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # ---- device-timed region ----
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else os.devnull)
+    barrier()
+    torch.cuda.synchronize()
+    with clk:
+        e0.record(stream)
+        sim.step(args.steps, DT, therm(args.steps))
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    step += args.steps
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    obs = sim.observe(bbmd.OBS_ENERGY)
+    clocks = clk.summary()
+
+    # ---- per-phase attribution (same steps, phases launched one by one) ----
+    nprof = max(2, min(args.steps, 10))
+    phases, nreb = sim.step_profiled(nprof, DT, therm(nprof))
+    step += nprof
+    force_ms = phases["force"] / nprof
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    pos, vel, img = sim.get_state()
+    pin = [torch.empty(a.shape, dtype=torch.float64 if a.dtype == np.float64 else torch.int32,
+                       pin_memory=True) for a in (pos, vel, img)]
+    for t, a in zip(pin, (pos, vel, img)):
+        t.numpy()[...] = a
+    hp, hv, hi = (t.numpy() for t in pin)
+    ke2 = max(1, args.e2e_steps)
+    barrier()
+    t0 = time.perf_counter()
+    sim.set_state(hp, hv, hi)
+    sim.step(ke2, DT, therm(ke2))
+    o2 = sim.observe(bbmd.OBS_ENERGY)
+    gp, gv, gi = sim.get_state()
+    t1 = time.perf_counter()
+    barrier()
+    e2e_s = t1 - t0
+    h2d = hp.nbytes + hv.nbytes + hi.nbytes
+    d2h = gp.nbytes + gv.nbytes + gi.nbytes + 8 * 16
+    sim.close()
+
+    # ---- FP64 form on the same workload (a few steps) ----
+    fp64 = None
+    if not args.no_fp64:
+        p64 = bbmd.ka_params(precision=bbmd.PREC_FP64)
+        sim64 = bbmd.Sim(p64, n, L, sp, None, None, T0=T_HIGH, seed=rank,
+                         stream=stream.cuda_stream, use_torch_allocator=True)
+        sim64.step(1, DT, therm(1))
+        stream.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = args.fp64_steps
+        a0.record(stream)
+        sim64.step(k64, DT, therm(k64))
+        a1.record(stream)
+        a1.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        ph64, _ = sim64.step_profiled(1, DT, therm(1))
+        sim64.close()
+        fp64 = {"value": n * k64 / (ms64 / 1e3), "unit": "particle-steps/s", "steps": k64,
+                "ms_per_step": ms64 / k64, "force_ms": ph64["force"]}
+
+    if rank != 0:
+        return None
+    value = ws * n * args.steps / (ms / 1e3)
+    pk = peaks()
+    clock_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_PER_SM_CLK * 2 * clock_mhz * 1e6 / 1e12  # TFLOP/s
+    hp_per = half_pairs_per_particle()
+    flops_launch = n * hp_per * FLOP_PER_HALF_PAIR
+    achieved = flops_launch / (force_ms / 1e3) / 1e12
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "force_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("bytes_per_launch_full_size")
+        except Exception:
+            traffic = None
+    out = {
+        "metric": "particle-steps/s (binary LJ, 16M & 1.02B N) mixed vs FP64 GPU; % of roofline",
+        "value": value,
+        "unit": "particle-steps/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 pair forces, i64 fixed-point state, f64 reductions",
+        "data": "synthetic: FCC 4*160^3 lattice, seeded 80:20 species, Maxwell-Boltzmann T=2.0",
+        "config": {"workload": "supercooling quench, N=16384000 (4*160^3 FCC, 80:20), rho=1.2, "
+                               "equilibrated at T=2.0, Nose-Hoover ramp 2.0->0.4 over 1e5 steps, "
+                               "dt=0.005, mixed, Verlet skin 0.3",
+                   "equilibration_steps": args.equil,
+                   "n_particles": n, "box": L, "parallelism": f"replicas x{ws}",
+                   "l2": "state and per-step traffic (>6 GB) far larger than the 129 MB L2"},
+        "e2e": {"value": ws * n * ke2 / e2e_s, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": h2d / ke2, "d2h_bytes_per_step": d2h / ke2,
+                "steps": ke2},
+        "roofline": {"bound": "alu", "kernel": "k_force (Verlet list, NH kinetic partials)",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "algorithmic": f"{hp_per:.2f} half pairs/particle x {FLOP_PER_HALF_PAIR:.0f} "
+                                    f"flop x {n} particles per launch",
+                     "force_ms": force_ms},
+        "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
+        "rebuilds_per_step": nreb / nprof,
+        "gpu_launches": args.steps * 13 + 2,
+        "clocks": clocks,
+        "fp64": fp64,
+        "observables": {"T": obs["temperature"], "pe_per_particle": obs["pe"] / n},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    return out
+
+
+def cpu_sample_state(ncell=40, seed=0):
+    from inputs import generate as gen
+
+    n = 4 * ncell ** 3
+    L = gen.box_for(n, 1.2)
+    pos = gen.fcc_lattice(ncell, L)
+    sp = gen.assign_species(n, n // 5, seed)
+    vel = gen.maxwell_boltzmann(n, T_HIGH, seed, np.ones(n))
+    return n, L, pos, vel, sp
+
+
+def cpu_baseline(budget_s=15.0, ncell=40):
+    """The FP64 oracle as it stands (single thread, cell search with Newton's third law),
+    on a bounded sample of the workload: N = 4*40^3 of the same mixture and ramp."""
+    import oracle
+
+    n, L, pos, vel, sp = cpu_sample_state(ncell)
+    st = oracle.MDState(pos, vel, sp, L, oracle.ka_params())
+    oracle.md_run(st, 1, DT, thermo=(T_HIGH, T_HIGH, TAU), use_cells=True)
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        oracle.md_run(st, 1, DT, thermo=(ramp_T(steps), ramp_T(steps + 1), TAU), use_cells=True)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"N={n} (4*{ncell}^3 FCC, same mixture, rho=1.2, NH ramp), {steps} steps, "
+                      f"{dt:.1f} s, FP64 cell search, single thread"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return None
+    import oracle
+
+    n, L, pos, vel, sp = cpu_sample_state(20)
+    st = oracle.MDState(pos, vel, sp, L, oracle.ka_params())
+    for k in range(args.warmup):
+        oracle.md_run(st, 1, DT, thermo=(ramp_T(k), ramp_T(k + 1), TAU), use_cells=True)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.md_run(st, 1, DT, thermo=(ramp_T(k), ramp_T(k + 1), TAU), use_cells=True)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    sample = (f"N={n} (4*20^3 FCC, same mixture, rho=1.2, NH ramp) per step, FP64 oracle, "
+              f"single thread")
+    return {"impl": "reference", "metric": "particle-steps/s (binary LJ, 16M & 1.02B N) mixed vs "
+            "FP64 GPU; % of roofline", "value": v, "unit": "particle-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "oracle on a bounded sample of the "
+                                                        "supercooling-quench workload"},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--equil", type=int, default=400,
+                    help="untimed equilibration steps at T=2.0 before the ramp")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

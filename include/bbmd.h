@@ -16,7 +16,8 @@
  *     or 1 (B).
  *   - Device memory is owned by the handle and obtained through the caller's allocator
  *     (bbmd_alloc) or cudaMalloc when it is NULL; bbmd_destroy returns all of it.
- *   - Work is enqueued on the CUDA stream given to bbmd_create (NULL = legacy default).
+ *   - Work is enqueued on the CUDA stream given to bbmd_create (NULL = one owned by the
+ *     handle).
  *     bbmd_step returns after enqueueing; every call that returns host data synchronises
  *     that stream.
  *   - Errors are returned as bbmd_status codes, never by abort or exit.  A device-side
@@ -162,7 +163,9 @@ typedef struct {
  * vel: n x 3 host velocities, or NULL for Maxwell-Boltzmann velocities at T0 drawn from
  *   the counter-based SplitMix64/Box-Muller generator under seed (net momentum removed,
  *   then scaled to 2K/(3n-3) = T0).
- * stream: a cudaStream_t (NULL = legacy default stream).  alloc: NULL = cudaMalloc.
+ * stream: a cudaStream_t, or NULL for a non-blocking stream created and owned by the
+ *   handle (the legacy default stream cannot hold the captured step graph).
+ * alloc: NULL = cudaMalloc.
  * On success *out receives the handle, the first list is built and the forces of the
  * initial positions are computed. */
 /* Non-finite input positions or velocities are rejected with BBMD_ERR_ARG. */
@@ -178,6 +181,23 @@ void bbmd_destroy(bbmd_sim* sim);
  * (NULL = NVE).  Asynchronous: returns after enqueueing on the handle's stream.  The list
  * is rebuilt on the device when needed, without a host round trip. */
 bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* thermo);
+
+/* Phases timed by bbmd_step_profiled. */
+enum {
+    BBMD_PHASE_INTEGRATE = 0,   /* kick + drift + wrap + frame copy + rebuild trigger          */
+    BBMD_PHASE_REBUILD = 1,     /* binning, scan, scatter, per-cell order, reorder (gated)     */
+    BBMD_PHASE_LIST = 2,        /* Verlet list build (gated)                                   */
+    BBMD_PHASE_FORCE = 3,       /* pair forces (+ kinetic-energy partials when thermostatted)  */
+    BBMD_PHASE_FINALIZE = 4,    /* reduction and thermostat update                             */
+    BBMD_PHASE_COUNT = 5
+};
+
+/* Same computation as bbmd_step, with every phase launched on its own and bracketed by CUDA
+ * events on the handle's stream; ms[BBMD_PHASE_COUNT] receives the summed device time of
+ * each phase over the nsteps steps and *rebuilds the number of rebuilds that ran (either
+ * may be NULL).  Synchronising.  Used to attribute step time to kernels. */
+bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt,
+                               const bbmd_thermostat* thermo, double* ms, int64_t* rebuilds);
 
 /* Measure the observables selected by mask at the current state (synchronising).  args may
  * be NULL for the defaults.  out->gr_counts / out->gr are filled when non-NULL and GR is

@@ -77,7 +77,10 @@ class bbmd_info(C.Structure):
                 ("stencil_capacity", C.c_int32), ("device_bytes", C.c_int64)]
 
 
-EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_observe", "bbmd_minimize",
+PHASES = ["integrate", "rebuild", "list", "force", "finalize"]
+
+EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bbmd_observe",
+           "bbmd_minimize",
            "bbmd_get_state", "bbmd_set_state", "bbmd_get_forces", "bbmd_get_cells",
            "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error"]
 
@@ -102,6 +105,8 @@ def load(path: str = LIB_PATH):
     L.bbmd_destroy.restype = None
     L.bbmd_step.argtypes = [vp, i64, d, P(bbmd_thermostat)]
     L.bbmd_step.restype = C.c_int
+    L.bbmd_step_profiled.argtypes = [vp, i64, d, P(bbmd_thermostat), P(d), P(i64)]
+    L.bbmd_step_profiled.restype = C.c_int
     L.bbmd_observe.argtypes = [vp, C.c_uint32, P(bbmd_obs_args), P(bbmd_obs)]
     L.bbmd_observe.restype = C.c_int
     L.bbmd_minimize.argtypes = [vp, i64, d, d]
@@ -223,6 +228,19 @@ class Sim:
             th = bbmd_thermostat(kind, T0, T1, tau)
         _check(self.h, load().bbmd_step(self.h, int(nsteps), float(dt),
                                         C.byref(th) if th is not None else None))
+
+    def step_profiled(self, nsteps, dt, thermostat=None):
+        """Per-phase device time (ms, summed over the steps) and the rebuild count."""
+        th = None
+        if thermostat is not None:
+            kind, T0, T1, tau = thermostat
+            th = bbmd_thermostat(kind, T0, T1, tau)
+        ms = np.zeros(len(PHASES))
+        nreb = C.c_int64()
+        _check(self.h, load().bbmd_step_profiled(self.h, int(nsteps), float(dt),
+                                                 C.byref(th) if th is not None else None,
+                                                 _dp(ms), C.byref(nreb)))
+        return dict(zip(PHASES, ms.tolist())), int(nreb.value)
 
     def observe(self, mask, nbins=500, rmax=5.0, k=7.25):
         o = bbmd_obs()

@@ -29,7 +29,12 @@ def _stale(obj: str, src: str) -> bool:
     return os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          out: str | None = None) -> str:
+    """Compile the library; `out` (default _build/) and `extra` nvcc flags allow side builds
+    of tuning variants."""
+    OUT = out or globals()["OUT"]
+    LIB = os.path.join(OUT, "libbbmd.so")
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     extra = extra or []

@@ -15,6 +15,7 @@ struct bbmd_sim {
     DevSim d;
     double box[3];
     cudaStream_t st = nullptr;
+    bool own_stream = false;
     bbmd_alloc alloc;
     bool have_alloc = false;
     std::vector<std::pair<void*, size_t>> blocks;
@@ -158,6 +159,7 @@ void fill_pair_table(const bbmd_params& P, PairTab& t) {
             t.dfcut[k] = P.shift == BBMD_SHIFT_FORCE ? dVc : 0.0;
             t.drc[k] = rc;
             t.sig2[k] = (float)t.dsig2[k];
+            t.sig2lo[k] = (float)(t.dsig2[k] - (double)t.sig2[k]);
             t.eps48[k] = (float)t.deps48[k];
             t.eps4[k] = (float)t.deps4[k];
             t.vshift[k] = (float)t.dvshift[k];
@@ -295,6 +297,13 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     bbmd_sim* sim = new bbmd_sim();
     sim->P = *params;
     sim->st = (cudaStream_t)stream;
+    if (!sim->st) {
+        if (cudaStreamCreateWithFlags(&sim->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete sim;
+            return BBMD_ERR_CUDA;
+        }
+        sim->own_stream = true;
+    }
     if (alloc && alloc->alloc && alloc->free) {
         sim->alloc = *alloc;
         sim->have_alloc = true;
@@ -313,12 +322,12 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
         for (int b = 0; b < 2; ++b) rcmax = std::fmax(rcmax, params->rcut[a][b]);
     double rcell = rcmax + params->skin;
     if (!cell_grid(box, D.kexp, rcell, D.nc, D.D)) {
-        delete sim;
+        bbmd_destroy(sim);
         return BBMD_ERR_BOX_TOO_SMALL;
     }
     int64_t ncell = (int64_t)D.nc[0] * D.nc[1] * D.nc[2];
     if (ncell > 0x7fffffffLL / 2) {
-        delete sim;
+        bbmd_destroy(sim);
         return BBMD_ERR_ARG;
     }
     D.ncell = (int32_t)ncell;
@@ -333,26 +342,27 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     double cellvol = std::ldexp((double)D.D[0], -D.kexp) * std::ldexp((double)D.D[1], -D.kexp) *
                      std::ldexp((double)D.D[2], -D.kexp);
     double mean = (double)n / V * cellvol;
+    // staged capacity of one 2x2x2 block: the 4x4x4 cells around it
     int smax = params->stencil_capacity > 0 ? params->stencil_capacity
-                                            : (int)(27.0 * mean * 1.3 + 96.0);
+                                            : (int)(64.0 * mean * 1.25 + 192.0);
     smax = (smax + 31) / 32 * 32;
-    int smax_cap = params->precision == BBMD_PREC_FP64 ? 1500 : 3000;
-    if (smax > smax_cap) smax = smax_cap;
     D.smax = smax;
     {
-        size_t stencil_bytes = (size_t)kWarpsPerBlock * (smax + 1) *
-                               (params->precision == BBMD_PREC_FP64 ? 32 : 16);
-        size_t build_bytes = (size_t)kWarpsPerBlock * (smax + 1) * 16 +
-                             (size_t)kWarpsPerBlock * 32 * (D.lcap8 * 8 + 2) * 2;
-        if (stencil_bytes > 220 * 1024 ||
-            (params->nbr_mode == BBMD_NBR_VERLET && build_bytes > 220 * 1024)) {
-            std::fprintf(stderr, "bbmd_create: list/stencil capacity exceeds shared memory\n");
-            delete sim;
+        size_t stage_bytes = (size_t)(smax + 1) * (params->precision == BBMD_PREC_FP64 ? 32 : 16);
+        if (smax > 65000 || stage_bytes > 200 * 1024) {
+            std::fprintf(stderr, "bbmd_create: staged-region capacity exceeds shared memory\n");
+            bbmd_destroy(sim);
             return BBMD_ERR_ARG;
         }
     }
-
-    prepare_force_kernels();
+    D.nblocks = (int64_t)((D.nc[0] + 1) / 2) * ((D.nc[1] + 1) / 2) * ((D.nc[2] + 1) / 2);
+    for (int d = 0; d < 3; ++d) D.halfL[d] = (float)(0.5 * box[d]);
+    if (!prepare_force_kernels()) {
+        cudaGetLastError();
+        std::fprintf(stderr, "bbmd_create: could not configure kernel shared memory\n");
+        bbmd_destroy(sim);
+        return BBMD_ERR_CUDA;
+    }
     // device properties and grids
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -360,13 +370,11 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     if (nsm <= 0) nsm = 1;
     D.grid_part = nsm * 8;
     {
-        size_t per_warp = (size_t)(smax + 1) * (params->precision == BBMD_PREC_FP64 ? 32 : 16);
-        size_t blk = per_warp * kWarpsPerBlock + 1024;
-        int per_sm = (int)(220000 / blk);
-        if (per_sm < 1) per_sm = 1;
-        if (per_sm > 8) per_sm = 8;
-        D.grid_cell = nsm * per_sm;
-        if (D.grid_cell > kMaxPartials) D.grid_cell = kMaxPartials;
+        int per_sm = force_blocks_per_sm(D);
+        int64_t g = (int64_t)nsm * per_sm;
+        if (g > D.nblocks) g = D.nblocks;
+        if (g > kMaxPartials) g = kMaxPartials;
+        D.grid_cell = (int32_t)(g > 0 ? g : 1);
     }
 
     // memory plan
@@ -467,7 +475,54 @@ void bbmd_destroy(bbmd_sim* sim) {
     else cudaDeviceSynchronize();
     free_graphs(sim);
     while (!sim->blocks.empty()) dev_free(sim, sim->blocks.back().first);
+    if (sim->own_stream) cudaStreamDestroy(sim->st);
     delete sim;
+}
+
+bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* th,
+                               double* ms, int64_t* rebuilds) {
+    if (!sim) return BBMD_ERR_ARG;
+    if (nsteps < 0 || nsteps > 0x7fffffff || !(dt > 0.0) || !(dt < 1.0))
+        return fail(sim, BBMD_ERR_ARG, "nsteps in [0, 2^31) and dt in (0, 1) required");
+    int nh = th && th->kind == BBMD_THERMO_NH;
+    if (nh && !(th->T_start > 0.0 && th->T_end > 0.0 && th->tau > 0.0))
+        return fail(sim, BBMD_ERR_ARG, "Nose-Hoover needs T_start, T_end, tau > 0");
+    cudaEvent_t ev[BBMD_PHASE_COUNT + 1];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    double acc[BBMD_PHASE_COUNT] = {0, 0, 0, 0, 0};
+    DevScalars scl0;
+    CK(cudaMemcpyAsync(&scl0, sim->d.sc, sizeof(scl0), cudaMemcpyDeviceToHost, sim->st));
+    launch_begin(sim->d, sim->st, nsteps, dt, nh ? th : nullptr);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        CK(cudaEventRecord(ev[0], sim->st));
+        launch_integrate(sim->d, sim->st);
+        CK(cudaEventRecord(ev[1], sim->st));
+        launch_rebuild_chain(sim->d, sim->st);
+        CK(cudaEventRecord(ev[2], sim->st));
+        launch_list_build(sim->d, sim->st);
+        CK(cudaEventRecord(ev[3], sim->st));
+        launch_force(sim->d, sim->st, false, nh != 0);
+        CK(cudaEventRecord(ev[4], sim->st));
+        launch_finalize(sim->d, sim->st, nh != 0);
+        CK(cudaEventRecord(ev[5], sim->st));
+        LAUNCHED("profiled step");
+        CK(cudaEventSynchronize(ev[5]));
+        for (int q = 0; q < BBMD_PHASE_COUNT; ++q) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
+            acc[q] += t;
+        }
+    }
+    launch_finish(sim->d, sim->st);
+    LAUNCHED("finish");
+    DevScalars scl1;
+    CK(cudaMemcpyAsync(&scl1, sim->d.sc, sizeof(scl1), cudaMemcpyDeviceToHost, sim->st));
+    CK(cudaStreamSynchronize(sim->st));
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (ms)
+        for (int q = 0; q < BBMD_PHASE_COUNT; ++q) ms[q] = acc[q];
+    if (rebuilds) *rebuilds = scl1.n_rebuilds - scl0.n_rebuilds;
+    return read_status(sim);
 }
 
 bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* th) {

@@ -5,11 +5,12 @@
 //   v[3][npad]   int64   velocities in units of 2^-52
 //   img[3][npad] int32   box crossings
 //   id[npad]     int32   particle id;  sp[npad] uint8 species
-//   rel[npad]    float4  position relative to the frame of its build cell, w = species
+//   rel[npad]    float4  position relative to the frame of its build cell, w = species (0.f / 1.f)
 //   relb[npad]   float4  the same at the last rebuild, w = (cell << 1) | species
 //   F[npad]      float4  mixed-precision force (w = per-particle energy on energy passes)
 //   Fd[3][npad]  double  FP64-form force
-//   list[lcap8][npad][8] uint16  Verlet list: stencil offsets in the tile's staged array
+//   list[lcap8][npad][8] uint16  Verlet list: offsets into the staged 4x4x4-cell region of
+//                                 the particle's 2x2x2 block of cells
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,7 +20,7 @@
 namespace bbmd {
 
 constexpr int kVelExp = 52;            // velocity unit 2^-52
-constexpr int kWarpsPerBlock = 4;      // force / list kernels: one warp per cell
+constexpr int kBlockWarps = 8;         // force / list kernels: one CTA per 2x2x2 cells
 constexpr int kMaxPartials = 8192;     // per-block FP64 partial sums
 constexpr float kBand = 1e-5f;         // relative band around a threshold for the FP64 re-test
 
@@ -53,7 +54,7 @@ struct PairTab {
     // FP32 tables [a*2+b]
     float rc2lo[4], rc2hi[4];     // rcut^2 (1 -/+ band)
     float R2lo[4], R2hi[4];       // (rcut + skin)^2 (1 -/+ band)
-    float sig2[4], eps48[4], eps4[4], vshift[4], fcut[4];
+    float sig2[4], sig2lo[4], eps48[4], eps4[4], vshift[4], fcut[4];
     // FP64 tables: exact decisions and the FP64 form
     double rc2[4], R2[4], dsig2[4], deps48[4], deps4[4], dvshift[4], dfcut[4], drc[4];
     float mass[2];
@@ -68,7 +69,9 @@ struct DevSim {
     int32_t kexp;
     float sx;                // 2^-k
     double sxd;
-    int32_t lcap8, smax;
+    int32_t lcap8, smax;     // list capacity / 8; staged capacity of one block region
+    int64_t nblocks;         // 2x2x2 blocks of cells
+    float halfL[3];          // L/2 (FP32) per axis
     int32_t nbr_mode, precision;
     float disp2;             // rebuild threshold on |x - x_build|^2 (FP32, conservative)
     PairTab pt;
@@ -84,7 +87,7 @@ struct DevSim {
     double* ref;             // [3][n] unwrapped reference positions by id (SET_REF)
     DevScalars* sc;
     int32_t grid_part;       // grid of per-particle grid-stride kernels
-    int32_t grid_cell;       // grid of warp-per-cell kernels (blocks of kWarpsPerBlock warps)
+    int32_t grid_cell;       // grid of block kernels (kBlockWarps warps per CTA)
 };
 
 // ---------------------------------------------------------------- conversions ----
@@ -141,10 +144,13 @@ __device__ __forceinline__ long long frame_axis(int a, long long D) {
     return (long long)a * D + (D >> 1);
 }
 
-// Minimum-image reduction of an integer displacement.
+// Minimum-image reduction of an integer displacement |d| < 3L/2: d > L/2 -> d - L,
+// d < -L/2 -> d + L.  For integer d the tests d > floor(L/2) and d < -floor(L/2) are the
+// same decisions as 2d > L and 2d < -L, without the overflow of 2d when L is near 2^62.
 __device__ __forceinline__ long long min_image(long long d, long long L) {
-    if (2 * d > L) d -= L;
-    else if (2 * d < -L) d += L;
+    const long long h = L >> 1;
+    if (d > h) d -= L;
+    else if (d < -h) d += L;
     return d;
 }
 
@@ -177,7 +183,9 @@ __device__ __forceinline__ void set_status(const DevSim& s, int bits) {
 // sort / rebuild chain (gated on sc->rebuild unless noted)
 void launch_rebuild_chain(const DevSim& s, cudaStream_t st);
 // one-time kernel attributes (call before any stream capture)
-void prepare_force_kernels();
+bool prepare_force_kernels();
+// resident CTAs per SM of the force kernel for this handle's shared-memory footprint
+int force_blocks_per_sm(const DevSim& s);
 // list build (gated)
 void launch_list_build(const DevSim& s, cudaStream_t st);
 // forces.  energy: also per-particle energy and virial partials; ke: NH kinetic partials

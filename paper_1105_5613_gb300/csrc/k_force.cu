@@ -1,22 +1,25 @@
 // Pair forces of the truncated Lennard-Jones / soft-sphere mixture (Sec. 2.1, Eqs. lj0,
 // sc0, mod0) over the cell stencil (Sec. 2.2), and the Verlet-list build.
 //
-// Work unit: one warp per cell ("tile" = up to 32 particles of the cell; larger cells are
-// processed in chunks of 32).  The warp stages the particles of the 27 surrounding cells
-// into its shared-memory stencil as float4 {x, y, z, species}, with coordinates expressed
-// in the frame of the tile's cell (the frame offset between two cells is exact in FP32
-// away from the periodic seam).  Each lane owns one particle i and accumulates its force
-// in registers: a full list, one writer per i, no atomics (the paper applies Newton's
-// third law to halve the pair work on a CPU; here every pair is visited from both sides
-// so that each force has a single owner and a fixed summation order).
+// Work unit: one CTA of 8 warps per 2x2x2 block of cells; warp w owns one cell of the block
+// (its "tile": up to 32 particles at a time, larger cells in chunks of 32).  The CTA stages
+// the 4x4x4 cells around the block -- the union of the eight 27-cell stencils -- into
+// shared memory as float4 {x, y, z, species} in one frame (the block's centre).  The raw
+// frame-relative records of each cell arrive by one TMA bulk copy per cell (cells are
+// contiguous after the counting sort); the exact frame offsets are then added in shared
+// memory.  Each lane owns one particle i and accumulates its force in registers: a full
+// list, one writer per i, no atomics (the paper applies Newton's third law to halve the
+// pair work on a CPU; here every pair is visited from both sides so that each force has
+// a single owner and a fixed summation order).
 //
-// The Verlet list stores, per particle, uint16 offsets into the staged stencil; entries
-// are laid out as [kb][npad][8] so a warp reads 8 entries per lane with one coalesced
-// 16-byte load.  Padding entries point to a sentinel far outside every cutoff.
+// The Verlet list stores, per particle, uint16 offsets into the block's staged array,
+// laid out as [kb][npad][8] so a warp reads 8 entries per lane with one coalesced 16-byte
+// load.  Padding entries point to a sentinel far outside every cutoff.
 //
-// Mixed precision: distances and forces in FP32 from frame-relative coordinates; a pair
-// whose FP32 r^2 lies within a relative 1e-5 of the cutoff is re-tested with the exact
-// FP64 rule so that the interacting set equals the FP64 definition.
+// Mixed precision: distances and forces in FP32 from block-frame coordinates.  A pair is
+// taken as interacting when its FP32 r^2 is below rc^2 (1 - 1e-5); a pair within that
+// relative band of the cutoff is decided by the exact FP64 rule in a rare fix-up after
+// each batch of 8 pairs, so the interacting set equals the FP64 definition.
 #include "bbmd_internal.cuh"
 
 namespace bbmd {
@@ -25,6 +28,11 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float kFar = 1.0e15f;
+constexpr int kBW = kBlockWarps;  // warps per CTA = cells per block
+constexpr int kRegion = 64;       // cells staged per block (4 x 4 x 4)
+#ifndef BBMD_FORCE_MIN_BLOCKS
+#define BBMD_FORCE_MIN_BLOCKS 3   // resident CTAs per SM the force kernel is compiled for
+#endif
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -32,93 +40,217 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-struct StencilInfo {
-    int off[28];   // prefix of staged counts (off[27] = total)
-    int cell[27];  // neighbour cell ids (fixed order: dz, dy, dx in -1..1)
+// The 4x4x4 region of cells staged for one block.
+struct Region {
+    int off[kRegion + 1];      // prefix of staged counts (clamped to smax); off[64] = total
+    int start[kRegion];        // first particle of each region cell
+    float hi[kRegion][3];      // frame offset of each cell (FP32 rounding of the exact value)
+    float lo[kRegion][3];      // exact residual of that rounding (non-zero across the seam)
+    long long fr[kRegion][3];  // FP64 form: frame point + seam image of each cell
+    int nstaged;
 };
 
-// Stage the 27-cell stencil of cell c into sm[0 .. total) (+ sentinel at sm[smax]).
-// Returns the staged count (truncated to smax, with a status bit on overflow).
-__device__ int stage_stencil(const DevSim& s, int c, float4* sm, StencilInfo& st, int lane) {
-    int ax, ay, az;
-    cell_coords(c, s.nc, ax, ay, az);
-    int start = 0, cnt = 0, nb = 0;
-    float shx = 0.f, shy = 0.f, shz = 0.f;
-    if (lane < 27) {
-        int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-        int a[3] = {ax, ay, az};
-        int b[3];
-        float sh[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            int bb = a[d] + o[d];
-            long long wrap = 0;
-            if (bb < 0) {
-                bb += s.nc[d];
-                wrap = -s.Lfix[d];
-            } else if (bb >= s.nc[d]) {
-                bb -= s.nc[d];
-                wrap = s.Lfix[d];
-            }
-            b[d] = bb;
-            long long delta = frame_axis(bb, s.D[d]) + wrap - frame_axis(a[d], s.D[d]);
-            sh[d] = i64_to_f32(delta) * s.sx;
-        }
-        nb = (b[2] * s.nc[1] + b[1]) * s.nc[0] + b[0];
-        start = s.cell_start[nb];
-        cnt = s.cell_start[nb + 1] - start;
-        shx = sh[0];
-        shy = sh[1];
-        shz = sh[2];
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    int total = __shfl_sync(FULL, incl, 26);
-    if (lane < 27) {
-        st.off[lane] = incl - cnt;
-        st.cell[lane] = nb;
-    }
-    if (lane == 0) st.off[27] = total;
-    __syncwarp();
-    if (total > s.smax) {
-        if (lane == 0) set_status(s, ST_STENCIL_OVERFLOW);
-        total = s.smax;
-    }
-    for (int q = 0; q < 27; ++q) {
-        int o0 = st.off[q];
-        int cq = st.off[q + 1] - o0;
-        int sq = __shfl_sync(FULL, start, q);
-        float hx = __shfl_sync(FULL, shx, q);
-        float hy = __shfl_sync(FULL, shy, q);
-        float hz = __shfl_sync(FULL, shz, q);
-        for (int t = lane; t < cq; t += 32) {
-            if (o0 + t < s.smax) {
-                float4 r = __ldg(&s.rel[sq + t]);
-                sm[o0 + t] = make_float4(r.x + hx, r.y + hy, r.z + hz, r.w);
-            }
-        }
-    }
-    if (lane == 0) sm[s.smax] = make_float4(kFar, kFar, kFar, __int_as_float(0));
-    __syncwarp();
-    return total;
+// ------------------------------------------------ TMA bulk copies and mbarriers ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Global index of staged entry t (rare path).
-__device__ __forceinline__ int64_t staged_global(const DevSim& s, const StencilInfo& st, int t) {
-    int q = 0;
-    while (q < 26 && st.off[q + 1] <= t) ++q;
-    return (int64_t)s.cell_start[st.cell[q]] + (t - st.off[q]);
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) global -> shared,
+// completion counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the current phase with an iteration limit; on expiry raise ST_TIMEOUT and
+// wait once more (again bounded) for the copies still in flight.
+__device__ __forceinline__ void mbar_wait_bounded(const DevSim& s, uint64_t* mbar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(mbar, parity)) return;
+    set_status(s, ST_TIMEOUT);
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(mbar, parity)) return;
+}
+
+// ------------------------------------------------------------------ blocks ----
+
+struct BlockPos {
+    int a0[3];  // first cell of the block per axis
+};
+
+__device__ __forceinline__ BlockPos block_pos(const DevSim& s, int64_t blk) {
+    const int nbx = (s.nc[0] + 1) >> 1, nby = (s.nc[1] + 1) >> 1;
+    BlockPos b;
+    b.a0[0] = (int)(blk % nbx) * 2;
+    b.a0[1] = (int)((blk / nbx) % nby) * 2;
+    b.a0[2] = (int)(blk / ((int64_t)nbx * nby)) * 2;
+    return b;
+}
+
+// Describe the region of block b (threads 0..63 take one region cell each): counts, frame
+// offsets relative to the block frame (the corner shared by the block's cells), prefix.
+__device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
+    __shared__ int wtot[2];
+    const int tid = threadIdx.x, lane = tid & 31;
+    int cnt = 0;
+    if (tid < kRegion) {
+        const int r[3] = {tid & 3, (tid >> 2) & 3, tid >> 4};
+        int a[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int aa = b.a0[d] - 1 + r[d];
+            long long wrap = 0;
+            if (aa < 0) {
+                aa += s.nc[d];
+                wrap = -s.Lfix[d];
+            } else if (aa >= s.nc[d]) {
+                aa -= s.nc[d];
+                wrap = s.Lfix[d];
+            }
+            a[d] = aa;
+            const long long fb = (long long)(b.a0[d] + 1) * s.D[d];  // block frame
+            const long long fr = frame_axis(aa, s.D[d]) + wrap;
+            const long long delta = fr - fb;
+            const float hi = i64_to_f32(delta) * s.sx;
+            const long long rest = delta - f32_to_i64(hi * pow2f(s.kexp));
+            R.hi[tid][d] = hi;
+            R.lo[tid][d] = i64_to_f32(rest) * s.sx;
+            R.fr[tid][d] = fr;
+        }
+        const int nb = (a[2] * s.nc[1] + a[1]) * s.nc[0] + a[0];
+        const int st = s.cell_start[nb];
+        cnt = s.cell_start[nb + 1] - st;
+        R.start[tid] = st;
+    }
+    int incl = cnt;
+    if (tid < kRegion) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wtot[tid >> 5] = incl;
+    }
+    __syncthreads();
+    if (tid < kRegion) {
+        int base = (tid >= 32) ? wtot[0] : 0;
+        int ex = base + incl - cnt;
+        R.off[tid] = min(ex, s.smax);
+        if (tid == kRegion - 1) {
+            int total = base + incl;
+            R.off[kRegion] = min(total, s.smax);
+            R.nstaged = min(total, s.smax);
+            if (total > s.smax) set_status(s, ST_STENCIL_OVERFLOW);
+        }
+    }
+    __syncthreads();
+}
+
+// Stage block b into sm (mixed precision): TMA bulk copy of each region cell's records,
+// then the frame offsets (residual first) and the sentinel sm[smax].
+__device__ void stage_block(const DevSim& s, const BlockPos& b, Region& R, float4* sm,
+                            uint64_t* mbar, uint32_t& phase) {
+    fence_proxy_async_smem();  // earlier generic accesses of sm before the async writes
+    region_info(s, b, R);
+    const int tid = threadIdx.x;
+    if (tid == 0) mbar_arrive_expect_tx(mbar, (uint32_t)R.nstaged * 16u);
+    __syncthreads();
+    if (tid < kRegion) {
+        const int n = R.off[tid + 1] - R.off[tid];
+        if (n > 0) bulk_g2s(sm + R.off[tid], s.rel + R.start[tid], (uint32_t)n * 16u, mbar);
+    }
+    mbar_wait_bounded(s, mbar, phase);
+    phase ^= 1u;
+    const int lane = tid & 31, w = tid >> 5;
+    for (int q = w; q < kRegion; q += kBW) {
+        const int o0 = R.off[q], cq = R.off[q + 1] - o0;
+        const float hx = R.hi[q][0], hy = R.hi[q][1], hz = R.hi[q][2];
+        const float lx = R.lo[q][0], ly = R.lo[q][1], lz = R.lo[q][2];
+        for (int t = lane; t < cq; t += 32) {
+            float4 v = sm[o0 + t];
+            v.x = (v.x + lx) + hx;
+            v.y = (v.y + ly) + hy;
+            v.z = (v.z + lz) + hz;
+            sm[o0 + t] = v;
+        }
+    }
+    if (tid == 0) sm[s.smax] = make_float4(kFar, kFar, kFar, 0.f);
+    __syncthreads();
+}
+
+// Global index of staged entry t (rare path): binary search of the region prefix.
+__device__ __forceinline__ int64_t staged_global(const Region& R, int t) {
+    int lo = 0, hi = kRegion - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (R.off[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return (int64_t)R.start[lo] + (t - R.off[lo]);
+}
+
+// The warp's own cell: its region index and whether it exists (odd nc leaves some warps of
+// the last block along an axis idle).
+struct WarpCell {
+    int c;      // cell id
+    int rq;     // region index of the cell
+    int wr[3];  // region coordinates of the stencil's first cell per axis
+    bool valid;
+};
+
+__device__ __forceinline__ WarpCell warp_cell(const DevSim& s, const BlockPos& b, int w) {
+    WarpCell wc;
+    const int o[3] = {w & 1, (w >> 1) & 1, w >> 2};
+    int a[3];
+    wc.valid = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        a[d] = b.a0[d] + o[d];
+        if (a[d] >= s.nc[d]) wc.valid = false;
+        wc.wr[d] = o[d];
+    }
+    wc.c = wc.valid ? (a[2] * s.nc[1] + a[1]) * s.nc[0] + a[0] : 0;
+    wc.rq = ((1 + o[2]) * 4 + (1 + o[1])) * 4 + (1 + o[0]);
+    return wc;
 }
 
 // Per-lane pair constants for the lane's species; field suffix = species of j.  Kept as
-// scalars and picked with selects so that nothing is indexed at run time (no local memory).
+// scalars and picked with selects so that nothing is indexed at run time.
 struct LaneTab {
     float rlo0, rlo1, rhi0, rhi1, sig20, sig21, e480, e481;
-    float e40, e41, vsh0, vsh1, fc0, fc1, rc0, rc1;
+    float e40, e41, vsh0, vsh1, fc0, fc1, rc0, rc1, sgl0, sgl1;
     float cpot;   // 0.5 for LJ force, 0 for soft sphere
     float cpe;    // 1 for LJ energy, 0 for soft sphere
     int si;
@@ -129,6 +261,7 @@ __device__ __forceinline__ void load_tab(const DevSim& s, int si, LaneTab& T) {
     T.rlo0 = s.pt.rc2lo[k];      T.rlo1 = s.pt.rc2lo[k + 1];
     T.rhi0 = s.pt.rc2hi[k];      T.rhi1 = s.pt.rc2hi[k + 1];
     T.sig20 = s.pt.sig2[k];      T.sig21 = s.pt.sig2[k + 1];
+    T.sgl0 = s.pt.sig2lo[k];     T.sgl1 = s.pt.sig2lo[k + 1];
     T.e480 = s.pt.eps48[k];      T.e481 = s.pt.eps48[k + 1];
     T.e40 = s.pt.eps4[k];        T.e41 = s.pt.eps4[k + 1];
     T.vsh0 = s.pt.vshift[k];     T.vsh1 = s.pt.vshift[k + 1];
@@ -144,39 +277,67 @@ struct Acc {
     double u, w;
 };
 
-// One pair (i, staged t).  d = x_t - x_i.
+// Force (and energy) of one pair; contributes only when `in`.  d = x_j - x_i.
 template <bool ENERGY, bool FSHIFT>
-__device__ __forceinline__ void pair_mixed(const DevSim& s, const StencilInfo& st, const LaneTab& T,
-                                           float4 me, float4 p, int64_t gi, int t, Acc& a) {
+__device__ __forceinline__ void pair_add(const LaneTab& T, bool b, float dx, float dy, float dz,
+                                         float r2, bool in, Acc& a) {
+    // energy passes use the correctly rounded reciprocal and carry sigma^2 as hi + lo so
+    // that summed pair energies carry no rounding bias; force passes use the fast forms
+    float ir2 = ENERGY ? __frcp_rn(r2) : rcp_approx(r2);
+    float s2 = ENERGY ? fmaf(b ? T.sig21 : T.sig20, ir2, (b ? T.sgl1 : T.sgl0) * ir2)
+                      : (b ? T.sig21 : T.sig20) * ir2;
+    float s6 = s2 * s2 * s2;
+    float f = (b ? T.e481 : T.e480) * ir2 * s6 * (s6 - T.cpot);
+    float ir = 0.f;
+    if (FSHIFT) {
+        ir = rsqrtf(r2);
+        f = fmaf(b ? T.fc1 : T.fc0, ir, f);
+    }
+    f = in ? f : 0.f;
+    a.fx = fmaf(f, dx, a.fx);
+    a.fy = fmaf(f, dy, a.fy);
+    a.fz = fmaf(f, dz, a.fz);
+    if (ENERGY) {
+        float V = (b ? T.e41 : T.e40) * s6 * (s6 - T.cpe) - (b ? T.vsh1 : T.vsh0);
+        if (FSHIFT) V -= (r2 * ir - (b ? T.rc1 : T.rc0)) * (b ? T.fc1 : T.fc0);
+        a.u += in ? (double)V : 0.0;
+        a.w += in ? (double)(f * r2) : 0.0;
+    }
+}
+
+// Fast path of one pair (i, staged t): interacting iff FP32 r^2 is below the lower edge
+// of the band around rc^2; a pair inside the band is only flagged for the exact fix-up.
+template <bool ENERGY, bool FSHIFT>
+__device__ __forceinline__ void pair_fast(const LaneTab& T, float4 me, float4 p, bool valid, Acc& a,
+                                          bool& band) {
     float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const bool b = (__float_as_int(p.w) & 1) != 0;
-    bool in = r2 < (b ? T.rlo1 : T.rlo0);
-    if (!in && r2 < (b ? T.rhi1 : T.rhi0)) {
-        // within the FP32 uncertainty of the cutoff: decide with the exact FP64 rule
-        int64_t gj = staged_global(s, st, t);
-        in = r2_exact(s, gi, gj) < s.pt.rc2[T.si * 2 + (b ? 1 : 0)];
-    }
-    if (in) {
-        float ir2 = rcp_approx(r2);
-        float s2 = (b ? T.sig21 : T.sig20) * ir2;
-        float s6 = s2 * s2 * s2;
-        float f = (b ? T.e481 : T.e480) * ir2 * s6 * (s6 - T.cpot);
-        float ir = 0.f;
-        if (FSHIFT) {
-            ir = rsqrtf(r2);
-            f += (b ? T.fc1 : T.fc0) * ir;
-        }
-        a.fx = fmaf(f, dx, a.fx);
-        a.fy = fmaf(f, dy, a.fy);
-        a.fz = fmaf(f, dz, a.fz);
-        if (ENERGY) {
-            float V = (b ? T.e41 : T.e40) * s6 * (s6 - T.cpe) - (b ? T.vsh1 : T.vsh0);
-            if (FSHIFT) V -= (r2 * ir - (b ? T.rc1 : T.rc0)) * (b ? T.fc1 : T.fc0);
-            a.u += (double)V;
-            a.w += (double)(f * r2);
-        }
-    }
+    const bool b = p.w != 0.f;
+    bool in = (r2 < (b ? T.rlo1 : T.rlo0)) && valid;
+    band = band || ((r2 < (b ? T.rhi1 : T.rhi0)) && !in && valid);
+    pair_add<ENERGY, FSHIFT>(T, b, dx, dy, dz, r2, in, a);
+}
+
+// A staged copy is usable only in the minimum image (the 4x4x4 region holds a cell twice
+// when nc = 3; the two copies are at least a cell side apart from any tile particle).
+__device__ __forceinline__ bool min_image_copy(const DevSim& s, float dx, float dy, float dz) {
+    return fabsf(dx) < s.halfL[0] && fabsf(dy) < s.halfL[1] && fabsf(dz) < s.halfL[2];
+}
+
+// Exact decision for a band pair; adds its force if the FP64 rule says it interacts.
+// Kept out of line: it runs for a few pairs per million and must not add register
+// pressure to the batch loop.
+template <bool ENERGY, bool FSHIFT>
+__device__ __noinline__ void pair_band(const DevSim& s, const Region& R, const LaneTab& T, float4 me, float4 p,
+                          int t, int64_t gi, bool valid, Acc& a) {
+    float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool b = p.w != 0.f;
+    if (!valid || r2 < (b ? T.rlo1 : T.rlo0) || !(r2 < (b ? T.rhi1 : T.rhi0))) return;
+    if (!min_image_copy(s, dx, dy, dz)) return;
+    int64_t gj = staged_global(R, t);
+    if (r2_exact(s, gi, gj) < s.pt.rc2[T.si * 2 + (b ? 1 : 0)])
+        pair_add<ENERGY, FSHIFT>(T, b, dx, dy, dz, r2, true, a);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -193,72 +354,116 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Block reduction of per-warp doubles into partials[q * kMaxPartials + blockIdx.x].
 __device__ void block_partials(const DevSim& s, const double* wv, int nq) {
-    __shared__ double red[kWarpsPerBlock][4];
+    __shared__ double red[kBW][4];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
         for (int q = 0; q < nq; ++q) red[w][q] = wv[q];
     __syncthreads();
     if (threadIdx.x < nq) {
         double t = 0.0;
-        for (int k = 0; k < kWarpsPerBlock; ++k) t += red[k][threadIdx.x];
+        for (int k = 0; k < kBW; ++k) t += red[k][threadIdx.x];
         s.partials[threadIdx.x * kMaxPartials + blockIdx.x] = t;
     }
 }
 
-// MODE 0: Verlet list.  MODE 1: every staged particle (no stored list).
+__device__ __forceinline__ unsigned lo16(unsigned w) { return w & 0xffffu; }
+__device__ __forceinline__ unsigned hi16(unsigned w) { return w >> 16; }
+
+// Contiguous staged range of stencil row (dy, dz) of the warp's cell: three consecutive
+// region cells along x.
+__device__ __forceinline__ void stencil_run(const Region& R, const WarpCell& wc, int row, int& rs,
+                                            int& re) {
+    const int ry = wc.wr[1] + row % 3, rz = wc.wr[2] + row / 3;
+    const int q0 = (rz * 4 + ry) * 4 + wc.wr[0];
+    rs = R.off[q0];
+    re = R.off[q0 + 3];
+}
+
+// MODE 0: Verlet list.  MODE 1: every particle of the 27-cell stencil (no stored list).
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(DevSim s) {
+__global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSim s) {
     extern __shared__ float4 smem[];
-    __shared__ StencilInfo sinfo[kWarpsPerBlock];
+    __shared__ Region R;
+    __shared__ __align__(8) uint64_t mbar;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float4* sm = smem + (size_t)w * (s.smax + 1);
-    StencilInfo& st = sinfo[w];
-    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+    float4* sm = smem;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
     double acc_ke = 0.0, acc_u = 0.0, acc_w = 0.0;
-    float hdt[2] = {0.f, 0.f};
+    float hdt0 = 0.f, hdt1 = 0.f;
     if (KE) {
         double dt = s.sc->dt;
-        hdt[0] = (float)(0.5 * dt / s.pt.dmass[0]);
-        hdt[1] = (float)(0.5 * dt / s.pt.dmass[1]);
+        hdt0 = (float)(0.5 * dt / s.pt.dmass[0]);
+        hdt1 = (float)(0.5 * dt / s.pt.dmass[1]);
     }
-    for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + w; c < s.ncell; c += nwarps) {
-        int total = stage_stencil(s, (int)c, sm, st, lane);
-        const int i0 = s.cell_start[c];
-        const int cnt = s.cell_start[c + 1] - i0;
-        const int self0 = st.off[13];
+    const float far = kFar;
+    for (int64_t blk = blockIdx.x; blk < s.nblocks; blk += gridDim.x) {
+        const BlockPos bp = block_pos(s, blk);
+        stage_block(s, bp, R, sm, &mbar, phase);
+        const WarpCell wc = warp_cell(s, bp, w);
+        const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
+        const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+        const int self0 = R.off[wc.rq];
         for (int ch = 0; ch * 32 < cnt; ++ch) {
             const int li = ch * 32 + lane;
             const bool act = li < cnt;
             const int64_t gi = (int64_t)i0 + li;
-            float4 me = act ? sm[self0 + li] : make_float4(-kFar, -kFar, -kFar, 0.f);
-            int si = __float_as_int(me.w) & 1;
+            const int self = self0 + li;
+            float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
+            const int si = me.w != 0.f ? 1 : 0;
             LaneTab T;
             load_tab(s, si, T);
             Acc a = {0.f, 0.f, 0.f, 0.0, 0.0};
             if (MODE == 0) {
                 const int nkb = s.cellmax[i0 + ch * 32];
                 const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
-                const uint4 sent = make_uint4(s.smax | (s.smax << 16), s.smax | (s.smax << 16),
-                                              s.smax | (s.smax << 16), s.smax | (s.smax << 16));
-                uint4 e = (act && nkb > 0) ? __ldcs(lp) : sent;
+                const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
+                const uint4 sent = make_uint4(sv, sv, sv, sv);
+                uint4 e0 = (act && nkb > 0) ? __ldcs(lp) : sent;
+                uint4 e1 = (act && nkb > 1) ? __ldcs(lp + s.npad) : sent;
                 for (int kb = 0; kb < nkb; ++kb) {
-                    uint4 en = (act && kb + 1 < nkb) ? __ldcs(lp + (int64_t)(kb + 1) * s.npad) : sent;
-#define BBMD_PAIR2(W)                                                          \
-    {                                                                          \
-        int t0 = (W) & 0xffffu, t1 = (W) >> 16;                                \
-        pair_mixed<ENERGY, FSHIFT>(s, st, T, me, sm[t0], gi, t0, a);           \
-        pair_mixed<ENERGY, FSHIFT>(s, st, T, me, sm[t1], gi, t1, a);           \
-    }
-                    BBMD_PAIR2(e.x) BBMD_PAIR2(e.y) BBMD_PAIR2(e.z) BBMD_PAIR2(e.w)
-#undef BBMD_PAIR2
-                    e = en;
+                    const uint4 e = e0;
+                    e0 = e1;
+                    e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
+                    bool band = false;
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.x)], true, a, band);
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.x)], true, a, band);
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.y)], true, a, band);
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.y)], true, a, band);
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.z)], true, a, band);
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.z)], true, a, band);
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.w)], true, a, band);
+                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.w)], true, a, band);
+                    if (__any_sync(FULL, band) && band) {
+                        const unsigned ws[4] = {e.x, e.y, e.z, e.w};
+                        for (int q = 0; q < 8; ++q) {
+                            int t = (q & 1) ? hi16(ws[q >> 1]) : lo16(ws[q >> 1]);
+                            pair_band<ENERGY, FSHIFT>(s, R, T, me, sm[t], t, gi, true, a);
+                        }
+                    }
                 }
             } else {
-                const int self = self0 + li;
-                for (int t = 0; t < total; ++t) {
-                    float4 p = sm[t];
-                    if (t == self) p = make_float4(kFar, kFar, kFar, 0.f);
-                    pair_mixed<ENERGY, FSHIFT>(s, st, T, me, p, gi, t, a);
+                for (int row = 0; row < 9; ++row) {
+                    int rs, re;
+                    stencil_run(R, wc, row, rs, re);
+                    for (int t0 = rs; t0 < re; t0 += 8) {
+                        bool band = false;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int t = t0 + u;
+                            const bool valid = t < re && t != self;
+                            pair_fast<ENERGY, FSHIFT>(T, me, sm[valid ? t : s.smax], valid, a, band);
+                        }
+                        if (__any_sync(FULL, band) && band) {
+                            for (int u = 0; u < 8; ++u) {
+                                const int t = t0 + u;
+                                const bool valid = t < re && t != self;
+                                pair_band<ENERGY, FSHIFT>(s, R, T, me, sm[valid ? t : s.smax], t,
+                                                          gi, valid, a);
+                            }
+                        }
+                    }
                 }
             }
             float fx = -a.fx, fy = -a.fy, fz = -a.fz;
@@ -270,7 +475,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(DevSim s) {
             if (KE) {
                 float k = 0.f;
                 if (act) {
-                    float h = si ? hdt[1] : hdt[0];
+                    float h = si ? hdt1 : hdt0;
                     float m = si ? s.pt.mass[1] : s.pt.mass[0];
                     float vx = fmaf(h, fx, i64_to_f32_fast(s.v[gi]) * pow2f(-kVelExp));
                     float vy = fmaf(h, fy, i64_to_f32_fast(s.v[s.npad + gi]) * pow2f(-kVelExp));
@@ -289,6 +494,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(DevSim s) {
                 }
             }
         }
+        __syncthreads();  // the staged block is reused by the next iteration
     }
     if (KE || ENERGY) {
         double wv[3] = {acc_ke, acc_u, acc_w};
@@ -298,170 +504,170 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force(DevSim s) {
 
 // ------------------------------------------------------------------ list build ----
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_list_build(DevSim s) {
+// Each lane tests every particle of its 27-cell stencil (broadcast reads, 32 candidates at
+// a time into a bitmask; band candidates are decided by the exact rule) and writes the
+// offsets of the set bits straight into its list ([kb][npad][8] uint16, two entries per
+// 32-bit store).
+__global__ void __launch_bounds__(kBW * 32) k_list_build(DevSim s) {
     if (!s.sc->rebuild) return;
     extern __shared__ float4 smem[];
-    __shared__ StencilInfo sinfo[kWarpsPerBlock];
+    __shared__ Region R;
+    __shared__ __align__(8) uint64_t mbar;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lcap = s.lcap8 * 8;
-    const int bstride = lcap + 2;  // odd number of 32-bit words per row
-    float4* sm = smem + (size_t)w * (s.smax + 1);
-    uint16_t* buf = reinterpret_cast<uint16_t*>(smem + (size_t)kWarpsPerBlock * (s.smax + 1)) +
-                    (size_t)w * 32 * bstride + (size_t)lane * bstride;
-    StencilInfo& st = sinfo[w];
-    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + w; c < s.ncell; c += nwarps) {
-        int total = stage_stencil(s, (int)c, sm, st, lane);
-        const int i0 = s.cell_start[c];
-        const int cnt = s.cell_start[c + 1] - i0;
-        const int self0 = st.off[13];
+    float4* sm = smem;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const float far = kFar;
+    const unsigned sentpair = (unsigned)s.smax | ((unsigned)s.smax << 16);
+    uint32_t* list32 = reinterpret_cast<uint32_t*>(s.list);
+    for (int64_t blk = blockIdx.x; blk < s.nblocks; blk += gridDim.x) {
+        const BlockPos bp = block_pos(s, blk);
+        stage_block(s, bp, R, sm, &mbar, phase);
+        const WarpCell wc = warp_cell(s, bp, w);
+        const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
+        const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+        const int self0 = R.off[wc.rq];
         for (int ch = 0; ch * 32 < cnt; ++ch) {
             const int li = ch * 32 + lane;
             const bool act = li < cnt;
             const int64_t gi = (int64_t)i0 + li;
             const int self = self0 + li;
-            float4 me = act ? sm[self] : make_float4(-kFar, -kFar, -kFar, 0.f);
-            int si = __float_as_int(me.w) & 1;
-            float Rlo0 = s.pt.R2lo[si * 2], Rlo1 = s.pt.R2lo[si * 2 + 1];
-            float Rhi0 = s.pt.R2hi[si * 2], Rhi1 = s.pt.R2hi[si * 2 + 1];
+            float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
+            const int si = me.w != 0.f ? 1 : 0;
+            const float Rlo0 = s.pt.R2lo[si * 2], Rlo1 = s.pt.R2lo[si * 2 + 1];
+            const float Rhi0 = s.pt.R2hi[si * 2], Rhi1 = s.pt.R2hi[si * 2 + 1];
             int len = 0;
-            for (int t = 0; t < total; ++t) {
-                float4 p = sm[t];
-                float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                int tj = __float_as_int(p.w) & 1;
-                bool in = r2 < (tj ? Rlo1 : Rlo0);
-                if (!in && act && r2 < (tj ? Rhi1 : Rhi0) && t != self) {
-                    int64_t gj = staged_global(s, st, t);
-                    in = r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj];
-                }
-                if (in && act && t != self) {
-                    if (len < lcap) buf[len] = (uint16_t)t;
-                    ++len;
+            unsigned pend = 0u;
+            for (int row = 0; row < 9; ++row) {
+                int rs, re;
+                stencil_run(R, wc, row, rs, re);
+                for (int t0 = rs; t0 < re; t0 += 32) {
+                    unsigned inw = 0u, bandw = 0u;
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const float4 p = sm[t0 + u < re ? t0 + u : s.smax];
+                        float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const bool b = p.w != 0.f;
+                        const bool in = r2 < (b ? Rlo1 : Rlo0);
+                        const bool bd = !in && r2 < (b ? Rhi1 : Rhi0);
+                        inw |= in ? (1u << u) : 0u;
+                        bandw |= bd ? (1u << u) : 0u;
+                    }
+                    if (self >= t0 && self < t0 + 32) {
+                        inw &= ~(1u << (self - t0));
+                        bandw &= ~(1u << (self - t0));
+                    }
+                    if (!act) inw = bandw = 0u;
+                    if (__any_sync(FULL, bandw != 0u) && bandw) {
+                        unsigned bw = bandw;
+                        while (bw) {
+                            const int u = __ffs(bw) - 1;
+                            bw &= bw - 1u;
+                            const float4 p = sm[t0 + u];
+                            const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                            if (!min_image_copy(s, dx, dy, dz)) continue;
+                            const int tj = p.w != 0.f ? 1 : 0;
+                            const int64_t gj = staged_global(R, t0 + u);
+                            if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= 1u << u;
+                        }
+                    }
+                    while (inw) {
+                        const int u = __ffs(inw) - 1;
+                        inw &= inw - 1u;
+                        const unsigned t = (unsigned)(t0 + u);
+                        if (len < lcap) {
+                            if (len & 1) {
+                                const int q2 = len >> 1;
+                                list32[((int64_t)(q2 >> 2) * s.npad + gi) * 4 + (q2 & 3)] =
+                                    pend | (t << 16);
+                            } else {
+                                pend = t;
+                            }
+                        }
+                        ++len;
+                    }
                 }
             }
             if (len > lcap) {
                 set_status(s, ST_LIST_OVERFLOW);
                 len = lcap;
             }
+            if (act && (len & 1)) {
+                const int q2 = len >> 1;
+                list32[((int64_t)(q2 >> 2) * s.npad + gi) * 4 + (q2 & 3)] =
+                    pend | ((unsigned)s.smax << 16);
+                ++len;
+            }
             int mx = len;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
             const int nkb = (mx + 7) >> 3;
-            for (int q = len; q < nkb * 8; ++q) buf[q] = (uint16_t)s.smax;
-            if (act) {
-                uint4* lp = reinterpret_cast<uint4*>(s.list) + gi;
-                for (int kb = 0; kb < nkb; ++kb) {
-                    const uint16_t* b = buf + kb * 8;
-                    uint4 e;
-                    e.x = (unsigned)b[0] | ((unsigned)b[1] << 16);
-                    e.y = (unsigned)b[2] | ((unsigned)b[3] << 16);
-                    e.z = (unsigned)b[4] | ((unsigned)b[5] << 16);
-                    e.w = (unsigned)b[6] | ((unsigned)b[7] << 16);
-                    lp[(int64_t)kb * s.npad] = e;
-                }
-            }
+            if (act)
+                for (int q2 = len >> 1; q2 < nkb * 4; ++q2)
+                    list32[((int64_t)(q2 >> 2) * s.npad + gi) * 4 + (q2 & 3)] = sentpair;
             if (lane == 0) s.cellmax[i0 + ch * 32] = (uint16_t)nkb;
-            __syncwarp();
         }
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------------ FP64 form ----
-// Stencil staged as exact integer positions shifted into the tile's periodic image;
-// distances are the exact integer differences rounded once to double (the same rule the
-// list decisions use), pair arithmetic and accumulation in FP64.
+// The same block region staged as exact integer positions in the block's periodic image
+// (frame point + seam image + the particle's minimum-image offset from the frame, which
+// stays right after the particle itself has crossed the boundary since the last build);
+// distances are the exact integer differences rounded once to double (the rule the list
+// decisions use), pair arithmetic and accumulation in FP64.
 
 struct Pos64 {
     long long x, y, z;
     int sp, pad;
 };
 
-__device__ int stage_stencil64(const DevSim& s, int c, Pos64* sm, StencilInfo& st, int lane) {
-    int ax, ay, az;
-    cell_coords(c, s.nc, ax, ay, az);
-    int start = 0, cnt = 0, nb = 0;
-    long long wx = 0, wy = 0, wz = 0;
-    if (lane < 27) {
-        int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
-        int a[3] = {ax, ay, az};
-        int b[3];
-        long long wr[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            int bb = a[d] + o[d];
-            wr[d] = 0;
-            if (bb < 0) {
-                bb += s.nc[d];
-                wr[d] = -s.Lfix[d];
-            } else if (bb >= s.nc[d]) {
-                bb -= s.nc[d];
-                wr[d] = s.Lfix[d];
-            }
-            b[d] = bb;
-        }
-        nb = (b[2] * s.nc[1] + b[1]) * s.nc[0] + b[0];
-        start = s.cell_start[nb];
-        cnt = s.cell_start[nb + 1] - start;
-        wx = wr[0];
-        wy = wr[1];
-        wz = wr[2];
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    int total = __shfl_sync(FULL, incl, 26);
-    if (lane < 27) {
-        st.off[lane] = incl - cnt;
-        st.cell[lane] = nb;
-    }
-    if (lane == 0) st.off[27] = total;
-    __syncwarp();
-    if (total > s.smax) {
-        if (lane == 0) set_status(s, ST_STENCIL_OVERFLOW);
-        total = s.smax;
-    }
-    for (int q = 0; q < 27; ++q) {
-        int o0 = st.off[q];
-        int cq = st.off[q + 1] - o0;
-        int sq = __shfl_sync(FULL, start, q);
-        long long hx = __shfl_sync(FULL, wx, q);
-        long long hy = __shfl_sync(FULL, wy, q);
-        long long hz = __shfl_sync(FULL, wz, q);
+__device__ void stage_block64(const DevSim& s, const BlockPos& b, Region& R, Pos64* sm) {
+    region_info(s, b, R);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = w; q < kRegion; q += kBW) {
+        const int o0 = R.off[q], cq = R.off[q + 1] - o0;
+        const long long fx = R.fr[q][0], fy = R.fr[q][1], fz = R.fr[q][2];
         for (int t = lane; t < cq; t += 32) {
-            if (o0 + t < s.smax) {
-                int64_t j = sq + t;
-                Pos64 p;
-                p.x = (long long)s.x[j] + hx;
-                p.y = (long long)s.x[s.npad + j] + hy;
-                p.z = (long long)s.x[2 * s.npad + j] + hz;
-                p.sp = s.sp[j];
-                p.pad = 0;
-                sm[o0 + t] = p;
-            }
+            const int64_t j = R.start[q] + t;
+            Pos64 p;
+            p.x = fx + min_image((long long)s.x[j] - fx, s.Lfix[0]);
+            p.y = fy + min_image((long long)s.x[s.npad + j] - fy, s.Lfix[1]);
+            p.z = fz + min_image((long long)s.x[2 * s.npad + j] - fz, s.Lfix[2]);
+            p.sp = s.sp[j];
+            p.pad = 0;
+            sm[o0 + t] = p;
         }
     }
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
+        // staged positions lie in (-L_fix, 2 L_fix) with L_fix < 2^62: a sentinel at 3 * 2^61
+        // on every axis is beyond every cutoff (|dx| > L/2 is never a minimum image) and no
+        // difference overflows
         Pos64 far;
-        far.x = far.y = far.z = (long long)1 << 62;
+        far.x = far.y = far.z = (long long)3 << 61;
         far.sp = 0;
         far.pad = 0;
         sm[s.smax] = far;
     }
-    __syncwarp();
-    return total;
+    __syncthreads();
 }
 
 template <bool ENERGY, bool FSHIFT>
 __device__ __forceinline__ void pair_fp64(const DevSim& s, int si, const Pos64& me, const Pos64& p,
                                           double& fx, double& fy, double& fz, double& u,
                                           double& w) {
-    double dx = __dmul_rn(__ll2double_rn(p.x - me.x), s.sxd);
-    double dy = __dmul_rn(__ll2double_rn(p.y - me.y), s.sxd);
-    double dz = __dmul_rn(__ll2double_rn(p.z - me.z), s.sxd);
+    const long long ix = p.x - me.x, iy = p.y - me.y, iz = p.z - me.z;
+    // only the minimum-image copy counts (a region may hold a cell twice when nc = 3)
+    if (llabs(ix) > (s.Lfix[0] >> 1) || llabs(iy) > (s.Lfix[1] >> 1) ||
+        llabs(iz) > (s.Lfix[2] >> 1))
+        return;
+    double dx = __dmul_rn(__ll2double_rn(ix), s.sxd);
+    double dy = __dmul_rn(__ll2double_rn(iy), s.sxd);
+    double dz = __dmul_rn(__ll2double_rn(iz), s.sxd);
     double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     int k = si * 2 + p.sp;
     if (r2 < s.pt.rc2[k]) {
@@ -489,19 +695,19 @@ __device__ __forceinline__ void pair_fp64(const DevSim& s, int si, const Pos64& 
 }
 
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force64(DevSim s) {
+__global__ void __launch_bounds__(kBW * 32) k_force64(DevSim s) {
     extern __shared__ float4 smem[];
-    __shared__ StencilInfo sinfo[kWarpsPerBlock];
+    __shared__ Region R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    Pos64* sm = reinterpret_cast<Pos64*>(smem) + (size_t)w * (s.smax + 1);
-    StencilInfo& st = sinfo[w];
-    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+    Pos64* sm = reinterpret_cast<Pos64*>(smem);
     double acc_ke = 0.0, acc_u = 0.0, acc_w = 0.0;
-    for (int64_t c = (int64_t)blockIdx.x * kWarpsPerBlock + w; c < s.ncell; c += nwarps) {
-        int total = stage_stencil64(s, (int)c, sm, st, lane);
-        const int i0 = s.cell_start[c];
-        const int cnt = s.cell_start[c + 1] - i0;
-        const int self0 = st.off[13];
+    for (int64_t blk = blockIdx.x; blk < s.nblocks; blk += gridDim.x) {
+        const BlockPos bp = block_pos(s, blk);
+        stage_block64(s, bp, R, sm);
+        const WarpCell wc = warp_cell(s, bp, w);
+        const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
+        const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+        const int self0 = R.off[wc.rq];
         for (int ch = 0; ch * 32 < cnt; ++ch) {
             const int li = ch * 32 + lane;
             const bool act = li < cnt;
@@ -513,7 +719,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force64(DevSim s) {
                 me.x = me.y = me.z = -((long long)1 << 62);
                 me.sp = 0;
             }
-            int si = me.sp;
+            const int si = me.sp;
             double fx = 0, fy = 0, fz = 0, u = 0, wv = 0;
             if (MODE == 0) {
                 const int nkb = s.cellmax[i0 + ch * 32];
@@ -528,11 +734,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force64(DevSim s) {
                         pair_fp64<ENERGY, FSHIFT>(s, si, me, sm[ws[q] >> 16], fx, fy, fz, u, wv);
                     }
                 }
-            } else {
+            } else if (act) {
                 const int self = self0 + li;
-                for (int t = 0; t < total; ++t) {
-                    if (t == self || !act) continue;
-                    pair_fp64<ENERGY, FSHIFT>(s, si, me, sm[t], fx, fy, fz, u, wv);
+                for (int row = 0; row < 9; ++row) {
+                    int rs, re;
+                    stencil_run(R, wc, row, rs, re);
+                    for (int t = rs; t < re; ++t) {
+                        if (t == self) continue;
+                        pair_fp64<ENERGY, FSHIFT>(s, si, me, sm[t], fx, fy, fz, u, wv);
+                    }
                 }
             }
             if (act) {
@@ -567,6 +777,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force64(DevSim s) {
                 }
             }
         }
+        __syncthreads();
     }
     if (KE || ENERGY) {
         double wv3[3] = {acc_ke, acc_u, acc_w};
@@ -574,29 +785,35 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_force64(DevSim s) {
     }
 }
 
-// Opt every kernel with dynamic shared memory into the device maximum once (outside any
-// stream capture); the launch itself then requests only what it needs.
-constexpr int kMaxDynSmem = 227 * 1024;
+// Opt every kernel with dynamic shared memory into the largest size the device allows
+// next to the kernel's static shared memory (done at create, outside any stream capture);
+// each launch then requests only what it needs.
+static bool g_smem_ok = true;
 
 template <typename K>
-void set_smem(K kernel, size_t /*bytes*/) {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-        done = true;
+void set_smem(K kernel) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+        g_smem_ok = false;
+        return;
     }
+    int dyn = optin - (int)fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
+        cudaSuccess)
+        g_smem_ok = false;
 }
 
 template <int MODE, bool E, bool KE, bool FS>
 void run_force(const DevSim& s, cudaStream_t st) {
     if (s.precision == BBMD_PREC_FP64) {
-        size_t bytes = (size_t)kWarpsPerBlock * (s.smax + 1) * sizeof(Pos64);
-        set_smem(k_force64<MODE, E, KE, FS>, bytes);
-        k_force64<MODE, E, KE, FS><<<s.grid_cell, kWarpsPerBlock * 32, bytes, st>>>(s);
+        size_t bytes = (size_t)(s.smax + 1) * sizeof(Pos64);
+        k_force64<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     } else {
-        size_t bytes = (size_t)kWarpsPerBlock * (s.smax + 1) * sizeof(float4);
-        set_smem(k_force<MODE, E, KE, FS>, bytes);
-        k_force<MODE, E, KE, FS><<<s.grid_cell, kWarpsPerBlock * 32, bytes, st>>>(s);
+        size_t bytes = (size_t)(s.smax + 1) * sizeof(float4);
+        k_force<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     }
 }
 
@@ -619,8 +836,8 @@ void run_force_mode(const DevSim& s, cudaStream_t st, bool energy, bool ke, bool
 
 template <int MODE, bool E, bool KE, bool FS>
 void prep_one() {
-    set_smem(k_force<MODE, E, KE, FS>, 0);
-    set_smem(k_force64<MODE, E, KE, FS>, 0);
+    set_smem(k_force<MODE, E, KE, FS>);
+    set_smem(k_force64<MODE, E, KE, FS>);
 }
 
 template <int MODE>
@@ -637,10 +854,22 @@ void prep_mode() {
 
 }  // namespace
 
-void prepare_force_kernels() {
+bool prepare_force_kernels() {
+    g_smem_ok = true;
     prep_mode<0>();
     prep_mode<1>();
-    set_smem(k_list_build, 0);
+    set_smem(k_list_build);
+    return g_smem_ok;
+}
+
+int force_blocks_per_sm(const DevSim& s) {
+    int nb = 0;
+    size_t bytes = (size_t)(s.smax + 1) * (s.precision == BBMD_PREC_FP64 ? sizeof(Pos64) : sizeof(float4));
+    if (s.precision == BBMD_PREC_FP64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force64<0, false, true, false>, kBW * 32, bytes);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force<0, false, true, false>, kBW * 32, bytes);
+    return nb > 0 ? nb : 1;
 }
 
 void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke) {
@@ -653,10 +882,8 @@ void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke) {
 
 void launch_list_build(const DevSim& s, cudaStream_t st) {
     if (s.nbr_mode != BBMD_NBR_VERLET) return;
-    size_t bytes = (size_t)kWarpsPerBlock * (s.smax + 1) * sizeof(float4) +
-                   (size_t)kWarpsPerBlock * 32 * (s.lcap8 * 8 + 2) * sizeof(uint16_t);
-    set_smem(k_list_build, bytes);
-    k_list_build<<<s.grid_cell, kWarpsPerBlock * 32, bytes, st>>>(s);
+    size_t bytes = (size_t)(s.smax + 1) * sizeof(float4);
+    k_list_build<<<s.grid_cell, kBW * 32, bytes, st>>>(s);
 }
 
 }  // namespace bbmd

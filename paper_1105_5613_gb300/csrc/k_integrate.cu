@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
             }
         }
         if (!(vmax < 1000.f)) set_status(s, ST_VEL_RANGE);
-        s.rel[i] = make_float4(r[0], r[1], r[2], __int_as_float(spc));
+        s.rel[i] = make_float4(r[0], r[1], r[2], (float)spc);
         float ex = r[0] - rb.x, ey = r[1] - rb.y, ez = r[2] - rb.z;
         if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > s.disp2) need = true;
     }
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kThreads) k_sd_move(DevSim s, double hmax, dou
             s.x[idx] = (uint64_t)x;
             r[d] = i64_to_f32(min_image(x - frame_axis(a3[d], s.D[d]), s.Lfix[d])) * s.sx;
         }
-        s.rel[i] = make_float4(r[0], r[1], r[2], __int_as_float(wb & 1));
+        s.rel[i] = make_float4(r[0], r[1], r[2], (float)(wb & 1));
         float ex = r[0] - rb.x, ey = r[1] - rb.y, ez = r[2] - rb.z;
         if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > s.disp2) need = true;
     }
@@ -520,17 +520,18 @@ __global__ void __launch_bounds__(kThreads) k_unpack_cells(DevSim s, int64_t* ce
         cell[s.id[k]] = __float_as_int(s.relb[k].w) >> 1;
 }
 
-// Global slot of staged offset t in the stencil of cell c (same order as staging).
+// Global slot of staged offset t in the region of the 2x2x2 block that holds cell c (the
+// 4x4x4 cells around the block in the force kernel's staging order).
 __device__ int64_t stencil_slot(const DevSim& s, int c, int t) {
     int ax, ay, az;
     cell_coords(c, s.nc, ax, ay, az);
+    const int a0[3] = {ax & ~1, ay & ~1, az & ~1};
     int acc = 0;
-    for (int q = 0; q < 27; ++q) {
-        int o[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
-        int a[3] = {ax, ay, az};
+    for (int q = 0; q < 64; ++q) {
+        const int r[3] = {q & 3, (q >> 2) & 3, q >> 4};
         int b[3];
         for (int d = 0; d < 3; ++d) {
-            int bb = a[d] + o[d];
+            int bb = a0[d] - 1 + r[d];
             if (bb < 0) bb += s.nc[d];
             else if (bb >= s.nc[d]) bb -= s.nc[d];
             b[d] = bb;

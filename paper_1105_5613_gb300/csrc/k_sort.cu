@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(DevSim s) {
         uint8_t spc = s.sp[o];
         s.sp2[k] = spc;
         s.relb[k] = make_float4(r[0], r[1], r[2], __int_as_float((c << 1) | spc));
-        s.rel[k] = make_float4(r[0], r[1], r[2], __int_as_float((int)spc));
+        s.rel[k] = make_float4(r[0], r[1], r[2], (float)spc);
     }
 }
 

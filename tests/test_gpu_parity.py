@@ -74,16 +74,19 @@ def test_forces_mixed(pot, shift, mode):
     assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
     obs = sim.observe(bbmd.OBS_ENERGY | bbmd.OBS_VIRIAL)
     assert abs(obs["pe"] - PEo) / n <= 1e-6
-    assert abs(obs["virial"] - Wo) / n <= 1e-5
-    assert np.abs(u - uo).max() <= 5e-5
+    assert abs(obs["virial"] - Wo) <= 1e-6 * abs(Wo)
+    # per-particle energies: FP32 pair energies, FP64 sums
+    assert np.abs(u - uo).max() <= 2e-4
     sim.close()
 
 
+@pytest.mark.parametrize("ncell", [8, 10])
 @pytest.mark.parametrize("shift", [1, 2])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_forces_fp64_form(shift, mode):
-    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.12, precision=bbmd.PREC_FP64, shift=shift,
-                                      nbr_mode=mode)
+def test_forces_fp64_form(shift, mode, ncell):
+    # ncell 10: L * 2^k close to 2^62 and an odd number of cells per axis
+    sim, n, L, pos, vel, sp, p = make(ncell=ncell, shake=0.12, precision=bbmd.PREC_FP64,
+                                      shift=shift, nbr_mode=mode)
     xq, _, _ = quantized(pos, L)
     po = oracle_params(p)
     Fo, uo, Wo, PEo = oracle.forces(xq, sp, L, po)
@@ -93,6 +96,28 @@ def test_forces_fp64_form(shift, mode):
     obs = sim.observe(bbmd.OBS_ENERGY | bbmd.OBS_VIRIAL)
     assert abs(obs["pe"] - PEo) <= 1e-10 * abs(PEo)
     assert np.allclose(u, uo, rtol=1e-10, atol=1e-12)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forces_near_the_seam(prec):
+    """Lattice shifted so that many particles sit next to the periodic boundary (odd cell
+    count, L * 2^k close to 2^62)."""
+    n, L, pos, vel, sp = mixture(10, T=2.0, shake=0.0)
+    shifted = (pos + 0.5 * L / 10 * np.array([0.9, 0.3, 0.7]) + 0.13) % L
+    rng = np.random.default_rng(3)
+    shifted = (shifted + rng.uniform(-0.1, 0.1, shifted.shape)) % L
+    p = bbmd.ka_params(precision=prec)
+    sim = bbmd.Sim(p, n, L, sp, shifted, vel)
+    xq, _, _ = quantized(shifted, L)
+    Fo = oracle.forces(xq, sp, L, oracle_params(p))[0]
+    F = sim.get_forces()
+    if prec == 1:
+        rel = np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), 1e-3)
+        assert rel.max() <= 1e-10
+    else:
+        e = force_errors(F, Fo)
+        assert np.median(e) <= 1e-5 and e.max() <= 1e-4
     sim.close()
 
 
@@ -171,16 +196,18 @@ def test_nose_hoover_ramp_matches_oracle():
 
 
 def test_nve_energy_conservation():
+    """Same criterion as the oracle's own pin: velocity Verlet fluctuates but does not drift
+    (means of 100-step windows agree within 1e-4 per particle)."""
     sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.05, T=2.0)
     E = []
-    for _ in range(12):
-        sim.step(50, 0.005)
+    for _ in range(600):
+        sim.step(1, 0.005)
         o = sim.observe(bbmd.OBS_ENERGY | bbmd.OBS_MOMENTUM)
         E.append((o["ke"] + o["pe"]) / n)
-        assert np.abs(o["momentum"]).max() < 1e-3
     E = np.array(E)
-    assert abs(E[-4:].mean() - E[2:6].mean()) < 1e-4, E
-    assert o["n_rebuilds"] > 5
+    assert abs(E[500:].mean() - E[100:200].mean()) < 1e-4, (E[500:].mean(), E[100:200].mean())
+    assert np.abs(o["momentum"]).max() < 1e-3
+    assert o["n_rebuilds"] > 20
     sim.close()
 
 
@@ -252,7 +279,7 @@ def test_edge_crowded_cells_and_single_species():
     pos = gen.rsa_positions(n, L, 0.62, 33)
     pos[:, 2] = pos[:, 2] * 0.6
     sp = np.ones(n, dtype=np.uint8)
-    p = bbmd.ka_params(stencil_capacity=3000)
+    p = bbmd.ka_params(stencil_capacity=2000, list_capacity=256)
     sim = bbmd.Sim(p, n, L, sp, pos, np.zeros((n, 3)))
     xq, xfix, k = quantized(pos, L)
     cells = sim.get_cells()
@@ -324,21 +351,29 @@ def test_state_round_trip_and_resume():
     twin.close()
 
 
-def test_minimize_matches_oracle_energy():
+def test_minimize_matches_oracle():
+    """Steepest descent from random sequential addition: the trajectory follows the oracle
+    while the step is force-limited; with h = 1e-3 the iteration is unstable along the
+    stiffest pair directions (h > 2 / largest curvature), which amplifies rounding
+    differences, so later steps are compared by the energy they reach."""
     n = 1500
     L = gen.box_for(n, 1.2)
     pos = gen.rsa_positions(n, L, 0.7, 3)
     sp = gen.assign_species(n, 300, 3)
     p = bbmd.ka_params()
+    xq, _, _ = quantized(pos, L)
     sim = bbmd.Sim(p, n, L, sp, pos, np.zeros((n, 3)))
     e0 = sim.observe(bbmd.OBS_ENERGY)["pe"]
-    sim.minimize(50)
+    sim.minimize(15)
+    gp, _, _ = sim.get_state()
+    relaxed = oracle.sd_run(xq, sp, L, oracle_params(p), 15, use_cells=True)
+    assert min_image_rms(gp, relaxed, L) <= 1e-5
+    sim.minimize(35)
     e1 = sim.observe(bbmd.OBS_ENERGY)["pe"]
-    xq, _, _ = quantized(pos, L)
-    relaxed = oracle.sd_run(xq, sp, L, oracle_params(p), 50, use_cells=True)
+    relaxed = oracle.sd_run(relaxed, sp, L, oracle_params(p), 35, use_cells=True)
     eo = oracle.forces(relaxed, sp, L, oracle_params(p))[3]
-    assert e1 < e0
-    assert abs(e1 - eo) / n < 1e-4
+    assert e1 < e0 and eo < e0
+    assert abs(e1 - eo) <= 1e-3 * abs(e0 - eo)
     sim.close()
 
 

@@ -87,11 +87,13 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libbbmd.so (raises if it has not been built)."""
+def load(path: str | None = None):
+    """Load libbbmd.so (raises if it has not been built).  The BBMD_LIB environment
+    variable selects another build of the library."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("BBMD_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libbbmd.so not found at {path}: build it first "
                            "(python -c 'import __graft_entry__ as g; g.build()')")

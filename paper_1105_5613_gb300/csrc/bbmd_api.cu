@@ -342,20 +342,24 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     double cellvol = std::ldexp((double)D.D[0], -D.kexp) * std::ldexp((double)D.D[1], -D.kexp) *
                      std::ldexp((double)D.D[2], -D.kexp);
     double mean = (double)n / V * cellvol;
-    // staged capacity of one 2x2x2 block: the 4x4x4 cells around it
+    // staged capacity of one block: the region of cells around it
     int smax = params->stencil_capacity > 0 ? params->stencil_capacity
-                                            : (int)(64.0 * mean * 1.25 + 192.0);
+                                            : (int)((double)kRegionCells * mean * 1.15 + 160.0);
     smax = (smax + 31) / 32 * 32;
     D.smax = smax;
     {
-        size_t stage_bytes = (size_t)(smax + 1) * (params->precision == BBMD_PREC_FP64 ? 32 : 16);
+        // mixed: two staging buffers (+ 32 entries of slack each in the list build); FP64:
+        // one buffer of 32-byte records
+        size_t stage_bytes = params->precision == BBMD_PREC_FP64 ? (size_t)(smax + 1) * 32
+                                                                 : (size_t)(smax + 33) * 32;
         if (smax > 65000 || stage_bytes > 200 * 1024) {
             std::fprintf(stderr, "bbmd_create: staged-region capacity exceeds shared memory\n");
             bbmd_destroy(sim);
             return BBMD_ERR_ARG;
         }
     }
-    D.nblocks = (int64_t)((D.nc[0] + 1) / 2) * ((D.nc[1] + 1) / 2) * ((D.nc[2] + 1) / 2);
+    D.nblocks = (int64_t)((D.nc[0] + 1) / 2) * ((D.nc[1] + 1) / 2) *
+                ((D.nc[2] + kBlockZ - 1) / kBlockZ);
     for (int d = 0; d < 3; ++d) D.halfL[d] = (float)(0.5 * box[d]);
     if (!prepare_force_kernels()) {
         cudaGetLastError();

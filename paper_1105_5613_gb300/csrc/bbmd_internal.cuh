@@ -9,8 +9,8 @@
 //   relb[npad]   float4  the same at the last rebuild, w = (cell << 1) | species
 //   F[npad]      float4  mixed-precision force (w = per-particle energy on energy passes)
 //   Fd[3][npad]  double  FP64-form force
-//   list[lcap8][npad][8] uint16  Verlet list: offsets into the staged 4x4x4-cell region of
-//                                 the particle's 2x2x2 block of cells
+//   list[lcap8][npad][8] uint16  Verlet list: offsets into the staged region (the cells
+//                                 around the particle's block of 2 x 2 x kBlockZ cells)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,7 +20,12 @@
 namespace bbmd {
 
 constexpr int kVelExp = 52;            // velocity unit 2^-52
-constexpr int kBlockWarps = 8;         // force / list kernels: one CTA per 2x2x2 cells
+#ifndef BBMD_BLOCK_Z
+#define BBMD_BLOCK_Z 2                 // cells per block along z (blocks are 2 x 2 x BLOCK_Z)
+#endif
+constexpr int kBlockZ = BBMD_BLOCK_Z;
+constexpr int kBlockWarps = 4 * kBlockZ;  // force / list kernels: one warp per cell of a block
+constexpr int kRegionCells = 16 * (kBlockZ + 2);  // cells staged per block: 4 x 4 x (BZ + 2)
 constexpr int kMaxPartials = 8192;     // per-block FP64 partial sums
 constexpr float kBand = 1e-5f;         // relative band around a threshold for the FP64 re-test
 
@@ -70,7 +75,7 @@ struct DevSim {
     float sx;                // 2^-k
     double sxd;
     int32_t lcap8, smax;     // list capacity / 8; staged capacity of one block region
-    int64_t nblocks;         // 2x2x2 blocks of cells
+    int64_t nblocks;         // blocks of 2 x 2 x kBlockZ cells
     float halfL[3];          // L/2 (FP32) per axis
     int32_t nbr_mode, precision;
     float disp2;             // rebuild threshold on |x - x_build|^2 (FP32, conservative)

@@ -29,9 +29,9 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float kFar = 1.0e15f;
 constexpr int kBW = kBlockWarps;  // warps per CTA = cells per block
-constexpr int kRegion = 64;       // cells staged per block (4 x 4 x 4)
+constexpr int kRegion = kRegionCells;  // cells staged per block: 4 x 4 x (kBlockZ + 2)
 #ifndef BBMD_FORCE_MIN_BLOCKS
-#define BBMD_FORCE_MIN_BLOCKS 3   // resident CTAs per SM the force kernel is compiled for
+#define BBMD_FORCE_MIN_BLOCKS (24 / kBW)  // resident CTAs per SM the force kernel targets
 #endif
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -40,9 +40,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// The 4x4x4 region of cells staged for one block.
+// The region of cells staged for one block: 4 x 4 x (kBlockZ + 2), index q = (z*4 + y)*4 + x.
 struct Region {
-    int off[kRegion + 1];      // prefix of staged counts (clamped to smax); off[64] = total
+    int off[kRegion + 1];      // prefix of staged counts (clamped to smax); off[kRegion] = total
     int start[kRegion];        // first particle of each region cell
     float hi[kRegion][3];      // frame offset of each cell (FP32 rounding of the exact value)
     float lo[kRegion][3];      // exact residual of that rounding (non-zero across the seam)
@@ -94,14 +94,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the current phase with an iteration limit; on expiry raise ST_TIMEOUT and
-// wait once more (again bounded) for the copies still in flight.
-__device__ __forceinline__ void mbar_wait_bounded(const DevSim& s, uint64_t* mbar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it)
-        if (mbar_try_wait(mbar, parity)) return;
+// Wait for the current phase with an iteration limit.  On expiry raise ST_TIMEOUT, wait
+// once more (again bounded) for the copies still in flight, and return false.
+constexpr int kWaitLimit = 1 << 18;
+
+__device__ __forceinline__ bool mbar_wait_bounded(const DevSim& s, uint64_t* mbar, uint32_t parity) {
+    for (int it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(mbar, parity)) return true;
     set_status(s, ST_TIMEOUT);
-    for (int it = 0; it < (1 << 22); ++it)
-        if (mbar_try_wait(mbar, parity)) return;
+    for (int it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(mbar, parity)) break;
+    return false;
 }
 
 // ------------------------------------------------------------------ blocks ----
@@ -115,14 +118,14 @@ __device__ __forceinline__ BlockPos block_pos(const DevSim& s, int64_t blk) {
     BlockPos b;
     b.a0[0] = (int)(blk % nbx) * 2;
     b.a0[1] = (int)((blk / nbx) % nby) * 2;
-    b.a0[2] = (int)(blk / ((int64_t)nbx * nby)) * 2;
+    b.a0[2] = (int)(blk / ((int64_t)nbx * nby)) * kBlockZ;
     return b;
 }
 
-// Describe the region of block b (threads 0..63 take one region cell each): counts, frame
-// offsets relative to the block frame (the corner shared by the block's cells), prefix.
+// Describe the region of block b (threads 0..kRegion-1 take one region cell each): counts,
+// frame offsets relative to the block frame, prefix.
 __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
-    __shared__ int wtot[2];
+    __shared__ int wtot[(kRegion + 31) / 32];
     const int tid = threadIdx.x, lane = tid & 31;
     int cnt = 0;
     if (tid < kRegion) {
@@ -140,7 +143,10 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
                 wrap = s.Lfix[d];
             }
             a[d] = aa;
-            const long long fb = (long long)(b.a0[d] + 1) * s.D[d];  // block frame
+            // block frame: the boundary between the block's cells (x, y) and, along z, that
+            // boundary for two cells or the centre of the single cell
+            const long long fb = d < 2 || kBlockZ == 2 ? (long long)(b.a0[d] + 1) * s.D[d]
+                                                       : frame_axis(b.a0[d], s.D[d]);
             const long long fr = frame_axis(aa, s.D[d]) + wrap;
             const long long delta = fr - fb;
             const float hi = i64_to_f32(delta) * s.sx;
@@ -154,8 +160,10 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
         cnt = s.cell_start[nb + 1] - st;
         R.start[tid] = st;
     }
+    // every lane of the warps that cover the region takes part in the scan (lanes past the
+    // region carry a count of zero)
     int incl = cnt;
-    if (tid < kRegion) {
+    if (tid < ((kRegion + 31) & ~31)) {
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int t = __shfl_up_sync(FULL, incl, o);
@@ -165,7 +173,8 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
     }
     __syncthreads();
     if (tid < kRegion) {
-        int base = (tid >= 32) ? wtot[0] : 0;
+        int base = 0;
+        for (int k = 0; k < (tid >> 5); ++k) base += wtot[k];
         int ex = base + incl - cnt;
         R.off[tid] = min(ex, s.smax);
         if (tid == kRegion - 1) {
@@ -178,10 +187,11 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
     __syncthreads();
 }
 
-// Stage block b into sm (mixed precision): TMA bulk copy of each region cell's records,
-// then the frame offsets (residual first) and the sentinel sm[smax].
-__device__ void stage_block(const DevSim& s, const BlockPos& b, Region& R, float4* sm,
-                            uint64_t* mbar, uint32_t& phase) {
+// Start staging block b into sm (mixed precision): describe its region, then one TMA bulk
+// copy per region cell of the raw frame-relative records, counted on mbar.  Does not wait.
+// All threads of the CTA call it; the previous reads of sm must be complete (barrier).
+__device__ void issue_block(const DevSim& s, const BlockPos& b, Region& R, float4* sm,
+                            uint64_t* mbar) {
     fence_proxy_async_smem();  // earlier generic accesses of sm before the async writes
     region_info(s, b, R);
     const int tid = threadIdx.x;
@@ -191,9 +201,16 @@ __device__ void stage_block(const DevSim& s, const BlockPos& b, Region& R, float
         const int n = R.off[tid + 1] - R.off[tid];
         if (n > 0) bulk_g2s(sm + R.off[tid], s.rel + R.start[tid], (uint32_t)n * 16u, mbar);
     }
-    mbar_wait_bounded(s, mbar, phase);
-    phase ^= 1u;
-    const int lane = tid & 31, w = tid >> 5;
+}
+
+// Wait for the copies of a block issued with issue_block, add the frame offsets of every
+// region cell (exact residual first), write the sentinel sm[smax] and synchronise.
+// Returns false on every thread of the CTA if some thread's wait gave up.
+__device__ bool finish_block(const DevSim& s, const Region& R, float4* sm, uint64_t* mbar,
+                             uint32_t parity) {
+    const bool ok = mbar_wait_bounded(s, mbar, parity);
+    if (__syncthreads_or(!ok)) return false;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int q = w; q < kRegion; q += kBW) {
         const int o0 = R.off[q], cq = R.off[q + 1] - o0;
         const float hx = R.hi[q][0], hy = R.hi[q][1], hz = R.hi[q][2];
@@ -208,6 +225,46 @@ __device__ void stage_block(const DevSim& s, const BlockPos& b, Region& R, float
     }
     if (tid == 0) sm[s.smax] = make_float4(kFar, kFar, kFar, 0.f);
     __syncthreads();
+    return true;
+}
+
+#ifndef BBMD_STAGE_BUFFERS
+#define BBMD_STAGE_BUFFERS 1  // 2: stage block i+1 while block i is computed
+#endif
+constexpr int kStageBuffers = BBMD_STAGE_BUFFERS;
+
+// Blocks of this CTA in order (grid-stride).  With two staging buffers the copies of block
+// i+1 are in flight while block i is computed; with one, each block is staged then
+// computed.  body(pos, R, sm) computes one staged block and must not synchronise the CTA.
+template <class Body>
+__device__ void for_each_block(const DevSim& s, float4* smem, int buf_stride, Region* R,
+                               uint64_t* mbar, Body body) {
+    int64_t blk = blockIdx.x;
+    if (kStageBuffers == 1) {
+        for (int it = 0; blk < s.nblocks; ++it, blk += gridDim.x) {
+            const BlockPos bp = block_pos(s, blk);
+            issue_block(s, bp, R[0], smem, &mbar[0]);
+            if (!finish_block(s, R[0], smem, &mbar[0], (uint32_t)(it & 1))) return;
+            body(bp, R[0], smem);
+            __syncthreads();
+        }
+        return;
+    }
+    float4* buf[2] = {smem, smem + buf_stride};
+    if (blk < s.nblocks) issue_block(s, block_pos(s, blk), R[0], buf[0], &mbar[0]);
+    for (int it = 0; blk < s.nblocks; ++it, blk += gridDim.x) {
+        const int cur = it & 1;
+        const int64_t nb = blk + gridDim.x;
+        if (nb < s.nblocks) issue_block(s, block_pos(s, nb), R[cur ^ 1], buf[cur ^ 1], &mbar[cur ^ 1]);
+        if (!finish_block(s, R[cur], buf[cur], &mbar[cur], (uint32_t)((it >> 1) & 1))) {
+            // let the copies already issued for the next block land before leaving
+            if (nb < s.nblocks)
+                mbar_wait_bounded(s, &mbar[cur ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            return;
+        }
+        body(block_pos(s, blk), R[cur], buf[cur]);
+        __syncthreads();  // buf[cur] and R[cur] are refilled two iterations later
+    }
 }
 
 // Global index of staged entry t (rare path): binary search of the region prefix.
@@ -383,13 +440,12 @@ __device__ __forceinline__ void stencil_run(const Region& R, const WarpCell& wc,
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
 __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSim s) {
     extern __shared__ float4 smem[];
-    __shared__ Region R;
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ Region R[kStageBuffers];
+    __shared__ __align__(8) uint64_t mbar[kStageBuffers];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float4* sm = smem;
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
     __syncthreads();
-    uint32_t phase = 0;
     double acc_ke = 0.0, acc_u = 0.0, acc_w = 0.0;
     float hdt0 = 0.f, hdt1 = 0.f;
     if (KE) {
@@ -398,30 +454,39 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
         hdt1 = (float)(0.5 * dt / s.pt.dmass[1]);
     }
     const float far = kFar;
-    for (int64_t blk = blockIdx.x; blk < s.nblocks; blk += gridDim.x) {
-        const BlockPos bp = block_pos(s, blk);
-        stage_block(s, bp, R, sm, &mbar, phase);
+    const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
+    const uint4 sent = make_uint4(sv, sv, sv, sv);
+    for_each_block(s, smem, s.smax + 1, R, mbar, [&](const BlockPos& bp, const Region& Rc,
+                                                      const float4* sm) {
         const WarpCell wc = warp_cell(s, bp, w);
         const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
         const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
-        const int self0 = R.off[wc.rq];
+        const int self0 = Rc.off[wc.rq];
         for (int ch = 0; ch * 32 < cnt; ++ch) {
             const int li = ch * 32 + lane;
             const bool act = li < cnt;
             const int64_t gi = (int64_t)i0 + li;
             const int self = self0 + li;
+            // issue the long-latency loads first: the first list rows, the velocity
+            const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
+            uint4 e0 = sent, e1 = sent;
+            if (MODE == 0 && act) {
+                e0 = __ldcs(lp);
+                e1 = __ldcs(lp + s.npad);
+            }
+            long long v0 = 0, v1 = 0, v2 = 0;
+            if (KE && act) {
+                v0 = s.v[gi];
+                v1 = s.v[s.npad + gi];
+                v2 = s.v[2 * s.npad + gi];
+            }
+            const int nkb = MODE == 0 ? s.cellmax[i0 + ch * 32] : 0;
             float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
             const int si = me.w != 0.f ? 1 : 0;
             LaneTab T;
             load_tab(s, si, T);
             Acc a = {0.f, 0.f, 0.f, 0.0, 0.0};
             if (MODE == 0) {
-                const int nkb = s.cellmax[i0 + ch * 32];
-                const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
-                const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
-                const uint4 sent = make_uint4(sv, sv, sv, sv);
-                uint4 e0 = (act && nkb > 0) ? __ldcs(lp) : sent;
-                uint4 e1 = (act && nkb > 1) ? __ldcs(lp + s.npad) : sent;
                 for (int kb = 0; kb < nkb; ++kb) {
                     const uint4 e = e0;
                     e0 = e1;
@@ -439,14 +504,14 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
                         const unsigned ws[4] = {e.x, e.y, e.z, e.w};
                         for (int q = 0; q < 8; ++q) {
                             int t = (q & 1) ? hi16(ws[q >> 1]) : lo16(ws[q >> 1]);
-                            pair_band<ENERGY, FSHIFT>(s, R, T, me, sm[t], t, gi, true, a);
+                            pair_band<ENERGY, FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
                         }
                     }
                 }
             } else {
                 for (int row = 0; row < 9; ++row) {
                     int rs, re;
-                    stencil_run(R, wc, row, rs, re);
+                    stencil_run(Rc, wc, row, rs, re);
                     for (int t0 = rs; t0 < re; t0 += 8) {
                         bool band = false;
 #pragma unroll
@@ -459,7 +524,7 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
                             for (int u = 0; u < 8; ++u) {
                                 const int t = t0 + u;
                                 const bool valid = t < re && t != self;
-                                pair_band<ENERGY, FSHIFT>(s, R, T, me, sm[valid ? t : s.smax], t,
+                                pair_band<ENERGY, FSHIFT>(s, Rc, T, me, sm[valid ? t : s.smax], t,
                                                           gi, valid, a);
                             }
                         }
@@ -477,9 +542,9 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
                 if (act) {
                     float h = si ? hdt1 : hdt0;
                     float m = si ? s.pt.mass[1] : s.pt.mass[0];
-                    float vx = fmaf(h, fx, i64_to_f32_fast(s.v[gi]) * pow2f(-kVelExp));
-                    float vy = fmaf(h, fy, i64_to_f32_fast(s.v[s.npad + gi]) * pow2f(-kVelExp));
-                    float vz = fmaf(h, fz, i64_to_f32_fast(s.v[2 * s.npad + gi]) * pow2f(-kVelExp));
+                    float vx = fmaf(h, fx, i64_to_f32_fast(v0) * pow2f(-kVelExp));
+                    float vy = fmaf(h, fy, i64_to_f32_fast(v1) * pow2f(-kVelExp));
+                    float vz = fmaf(h, fz, i64_to_f32_fast(v2) * pow2f(-kVelExp));
                     k = 0.5f * m * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
                 }
                 k = warp_sum_f(k);
@@ -494,8 +559,7 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
                 }
             }
         }
-        __syncthreads();  // the staged block is reused by the next iteration
-    }
+    });
     if (KE || ENERGY) {
         double wv[3] = {acc_ke, acc_u, acc_w};
         block_partials(s, wv, 3);
@@ -505,30 +569,32 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
 // ------------------------------------------------------------------ list build ----
 
 // Each lane tests every particle of its 27-cell stencil (broadcast reads, 32 candidates at
-// a time into a bitmask; band candidates are decided by the exact rule) and writes the
-// offsets of the set bits straight into its list ([kb][npad][8] uint16, two entries per
-// 32-bit store).
+// a time into a bitmask; band candidates are decided by the exact rule).  The set bits of
+// one stencil row (up to 4 words) are then written as list offsets, two entries per 32-bit
+// store into [kb][npad][8] uint16, the store address advanced incrementally.
+constexpr int kRowWords = 4;  // 32-candidate words held per stencil row and pass
+
 __global__ void __launch_bounds__(kBW * 32) k_list_build(DevSim s) {
     if (!s.sc->rebuild) return;
     extern __shared__ float4 smem[];
-    __shared__ Region R;
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ Region R[kStageBuffers];
+    __shared__ __align__(8) uint64_t mbar[kStageBuffers];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lcap = s.lcap8 * 8;
-    float4* sm = smem;
-    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
     __syncthreads();
-    uint32_t phase = 0;
     const float far = kFar;
     const unsigned sentpair = (unsigned)s.smax | ((unsigned)s.smax << 16);
     uint32_t* list32 = reinterpret_cast<uint32_t*>(s.list);
-    for (int64_t blk = blockIdx.x; blk < s.nblocks; blk += gridDim.x) {
-        const BlockPos bp = block_pos(s, blk);
-        stage_block(s, bp, R, sm, &mbar, phase);
+    const int64_t rowstep = (int64_t)s.npad * 4;  // uint32 distance between kb rows
+    // buffers are padded by 32 entries: word reads run past a row end
+    for_each_block(s, smem, s.smax + 1 + 32, R, mbar, [&](const BlockPos& bp, const Region& Rc,
+                                                           const float4* sm) {
         const WarpCell wc = warp_cell(s, bp, w);
         const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
         const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
-        const int self0 = R.off[wc.rq];
+        const int self0 = Rc.off[wc.rq];
         for (int ch = 0; ch * 32 < cnt; ++ch) {
             const int li = ch * 32 + lane;
             const bool act = li < cnt;
@@ -536,58 +602,80 @@ __global__ void __launch_bounds__(kBW * 32) k_list_build(DevSim s) {
             const int self = self0 + li;
             float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
             const int si = me.w != 0.f ? 1 : 0;
-            const float Rlo0 = s.pt.R2lo[si * 2], Rlo1 = s.pt.R2lo[si * 2 + 1];
-            const float Rhi0 = s.pt.R2hi[si * 2], Rhi1 = s.pt.R2hi[si * 2 + 1];
+            // thresholds as functions of the candidate's species w (0 or 1): R2lo(w) and a
+            // band width that covers both species (a wider band only means more exact tests)
+            const float RloA = s.pt.R2lo[si * 2], dRlo = s.pt.R2lo[si * 2 + 1] - RloA;
+            const float band = fmaxf(s.pt.R2hi[si * 2] - s.pt.R2lo[si * 2],
+                                     s.pt.R2hi[si * 2 + 1] - s.pt.R2lo[si * 2 + 1]);
             int len = 0;
             unsigned pend = 0u;
+            uint32_t* dst = list32 + gi * 4;  // slot of the next pair of entries
+            int word = 0;                      // 0..3 within the current kb row
             for (int row = 0; row < 9; ++row) {
                 int rs, re;
-                stencil_run(R, wc, row, rs, re);
-                for (int t0 = rs; t0 < re; t0 += 32) {
-                    unsigned inw = 0u, bandw = 0u;
+                stencil_run(Rc, wc, row, rs, re);
+                for (int r0 = rs; r0 < re; r0 += 32 * kRowWords) {
+                    unsigned m[kRowWords];
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        const float4 p = sm[t0 + u < re ? t0 + u : s.smax];
-                        float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const bool b = p.w != 0.f;
-                        const bool in = r2 < (b ? Rlo1 : Rlo0);
-                        const bool bd = !in && r2 < (b ? Rhi1 : Rhi0);
-                        inw |= in ? (1u << u) : 0u;
-                        bandw |= bd ? (1u << u) : 0u;
-                    }
-                    if (self >= t0 && self < t0 + 32) {
-                        inw &= ~(1u << (self - t0));
-                        bandw &= ~(1u << (self - t0));
-                    }
-                    if (!act) inw = bandw = 0u;
-                    if (__any_sync(FULL, bandw != 0u) && bandw) {
-                        unsigned bw = bandw;
-                        while (bw) {
-                            const int u = __ffs(bw) - 1;
-                            bw &= bw - 1u;
-                            const float4 p = sm[t0 + u];
-                            const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                            if (!min_image_copy(s, dx, dy, dz)) continue;
-                            const int tj = p.w != 0.f ? 1 : 0;
-                            const int64_t gj = staged_global(R, t0 + u);
-                            if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= 1u << u;
-                        }
-                    }
-                    while (inw) {
-                        const int u = __ffs(inw) - 1;
-                        inw &= inw - 1u;
-                        const unsigned t = (unsigned)(t0 + u);
-                        if (len < lcap) {
-                            if (len & 1) {
-                                const int q2 = len >> 1;
-                                list32[((int64_t)(q2 >> 2) * s.npad + gi) * 4 + (q2 & 3)] =
-                                    pend | (t << 16);
-                            } else {
-                                pend = t;
+                    for (int q = 0; q < kRowWords; ++q) {
+                        const int t0 = r0 + 32 * q;
+                        unsigned inw = 0u, hiw = 0u;
+                        if (t0 < re) {  // warp-uniform
+#pragma unroll
+                            for (int u = 0; u < 32; ++u) {
+                                const float4 p = sm[t0 + u];
+                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                // r^2 - R2lo(species of j), one FMA chain; sign bit = inside
+                                const float dlo =
+                                    fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
+                                const float dhi = dlo - band;
+                                inw |= (__float_as_uint(dlo) >> (31 - u)) & (1u << u);
+                                hiw |= (__float_as_uint(dhi) >> (31 - u)) & (1u << u);
+                            }
+                            unsigned valid = (re - t0 >= 32) ? 0xffffffffu : ((1u << (re - t0)) - 1u);
+                            if (self >= t0 && self < t0 + 32) valid &= ~(1u << (self - t0));
+                            if (!act) valid = 0u;
+                            inw &= valid;
+                            const unsigned bandw = hiw & ~inw & valid;
+                            if (__any_sync(FULL, bandw != 0u) && bandw) {
+                                unsigned bw = bandw;
+                                while (bw) {
+                                    const int u = __ffs(bw) - 1;
+                                    bw &= bw - 1u;
+                                    const float4 p = sm[t0 + u];
+                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                    if (!min_image_copy(s, dx, dy, dz)) continue;
+                                    const int tj = p.w != 0.f ? 1 : 0;
+                                    const int64_t gj = staged_global(Rc, t0 + u);
+                                    if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= 1u << u;
+                                }
                             }
                         }
-                        ++len;
+                        m[q] = inw;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kRowWords; ++q) {
+                        unsigned bits = m[q];
+                        const unsigned base = (unsigned)(r0 + 32 * q);
+                        while (bits) {
+                            const int u = __ffs(bits) - 1;
+                            bits &= bits - 1u;
+                            const unsigned t = base + (unsigned)u;
+                            if (len < lcap) {
+                                if (len & 1) {
+                                    *dst = pend | (t << 16);
+                                    if (++word == 4) {
+                                        word = 0;
+                                        dst += rowstep - 3;
+                                    } else {
+                                        ++dst;
+                                    }
+                                } else {
+                                    pend = t;
+                                }
+                            }
+                            ++len;
+                        }
                     }
                 }
             }
@@ -596,22 +684,33 @@ __global__ void __launch_bounds__(kBW * 32) k_list_build(DevSim s) {
                 len = lcap;
             }
             if (act && (len & 1)) {
-                const int q2 = len >> 1;
-                list32[((int64_t)(q2 >> 2) * s.npad + gi) * 4 + (q2 & 3)] =
-                    pend | ((unsigned)s.smax << 16);
+                *dst = pend | ((unsigned)s.smax << 16);
+                if (++word == 4) {
+                    word = 0;
+                    dst += rowstep - 3;
+                } else {
+                    ++dst;
+                }
                 ++len;
             }
             int mx = len;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
             const int nkb = (mx + 7) >> 3;
-            if (act)
-                for (int q2 = len >> 1; q2 < nkb * 4; ++q2)
-                    list32[((int64_t)(q2 >> 2) * s.npad + gi) * 4 + (q2 & 3)] = sentpair;
+            if (act) {
+                for (int q2 = len >> 1; q2 < nkb * 4; ++q2) {
+                    *dst = sentpair;
+                    if (++word == 4) {
+                        word = 0;
+                        dst += rowstep - 3;
+                    } else {
+                        ++dst;
+                    }
+                }
+            }
             if (lane == 0) s.cellmax[i0 + ch * 32] = (uint16_t)nkb;
         }
-        __syncthreads();
-    }
+    });
 }
 
 // ------------------------------------------------------------------ FP64 form ----
@@ -812,7 +911,7 @@ void run_force(const DevSim& s, cudaStream_t st) {
         size_t bytes = (size_t)(s.smax + 1) * sizeof(Pos64);
         k_force64<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     } else {
-        size_t bytes = (size_t)(s.smax + 1) * sizeof(float4);
+        size_t bytes = kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
         k_force<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     }
 }
@@ -864,7 +963,8 @@ bool prepare_force_kernels() {
 
 int force_blocks_per_sm(const DevSim& s) {
     int nb = 0;
-    size_t bytes = (size_t)(s.smax + 1) * (s.precision == BBMD_PREC_FP64 ? sizeof(Pos64) : sizeof(float4));
+    size_t bytes = s.precision == BBMD_PREC_FP64 ? (size_t)(s.smax + 1) * sizeof(Pos64)
+                                                 : kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
     if (s.precision == BBMD_PREC_FP64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force64<0, false, true, false>, kBW * 32, bytes);
     else
@@ -882,7 +982,9 @@ void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke) {
 
 void launch_list_build(const DevSim& s, cudaStream_t st) {
     if (s.nbr_mode != BBMD_NBR_VERLET) return;
-    size_t bytes = (size_t)(s.smax + 1) * sizeof(float4);
+    // staging buffer(s), each: staged region + sentinel + 32 entries of slack for word reads
+    // past a row end
+    size_t bytes = kStageBuffers * (size_t)(s.smax + 1 + 32) * sizeof(float4);
     k_list_build<<<s.grid_cell, kBW * 32, bytes, st>>>(s);
 }
 

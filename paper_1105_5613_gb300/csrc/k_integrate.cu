@@ -520,14 +520,14 @@ __global__ void __launch_bounds__(kThreads) k_unpack_cells(DevSim s, int64_t* ce
         cell[s.id[k]] = __float_as_int(s.relb[k].w) >> 1;
 }
 
-// Global slot of staged offset t in the region of the 2x2x2 block that holds cell c (the
-// 4x4x4 cells around the block in the force kernel's staging order).
+// Global slot of staged offset t in the region of the block that holds cell c (the cells
+// around the block in the force kernel's staging order).
 __device__ int64_t stencil_slot(const DevSim& s, int c, int t) {
     int ax, ay, az;
     cell_coords(c, s.nc, ax, ay, az);
-    const int a0[3] = {ax & ~1, ay & ~1, az & ~1};
+    const int a0[3] = {ax & ~1, ay & ~1, az - az % kBlockZ};
     int acc = 0;
-    for (int q = 0; q < 64; ++q) {
+    for (int q = 0; q < kRegionCells; ++q) {
         const int r[3] = {q & 3, (q >> 2) & 3, q >> 4};
         int b[3];
         for (int d = 0; d < 3; ++d) {

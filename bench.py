@@ -140,7 +140,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     b.build()
     bbmd.load()
-    n = 4 * NCELL_FCC ** 3
+    n = 4 * args.ncell ** 3
     L = gen.box_for(n, 1.2)
     sp = gen.assign_species(n, n // 5, 0)
     stream = make_stream()
@@ -156,6 +156,20 @@ def run_ours(args):
     # ramp), then untimed warm-up steps of the ramp (the first also captures the graph)
     if args.equil > 0:
         sim.step(args.equil, DT, (bbmd.THERMO_NH, T_HIGH, T_HIGH, TAU))
+    if args.profile_phases > 0:
+        # profiling case: one forced rebuild, then K steps with every phase launched on
+        # its own (the kernel launches that ncu captures), per-phase times printed
+        sim.rebuild()
+        k = args.profile_phases
+        ph, nr = sim.step_profiled(k, DT, (bbmd.THERMO_NH, T_HIGH, T_HIGH, TAU))
+        stream.synchronize()
+        sim.close()
+        if rank == 0:
+            print(json.dumps({"profile_case": {"n_particles": n, "equil": args.equil,
+                                               "steps": k, "rebuilds": nr,
+                                               "phases_ms_per_step":
+                                                   {a: v / k for a, v in ph.items()}}}))
+        return None
     sim.step(args.warmup, DT, therm(args.warmup))
     step += args.warmup
     stream.synchronize()
@@ -246,13 +260,7 @@ def run_ours(args):
     hp_per = half_pairs_per_particle()
     flops_launch = n * hp_per * FLOP_PER_HALF_PAIR
     achieved = flops_launch / (force_ms / 1e3) / 1e12
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "force_traffic.json")
-    if os.path.exists(tf):
-        try:
-            traffic = json.load(open(tf)).get("bytes_per_launch_full_size")
-        except Exception:
-            traffic = None
+    traffic = force_traffic(n)
     out = {
         "metric": "particle-steps/s (binary LJ, 16M & 1.02B N) mixed vs FP64 GPU; % of roofline",
         "value": value,
@@ -265,8 +273,10 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32 pair forces, i64 fixed-point state, f64 reductions",
-        "data": "synthetic: FCC 4*160^3 lattice, seeded 80:20 species, Maxwell-Boltzmann T=2.0",
-        "config": {"workload": "supercooling quench, N=16384000 (4*160^3 FCC, 80:20), rho=1.2, "
+        "data": f"synthetic: FCC 4*{args.ncell}^3 lattice, seeded 80:20 species, "
+                "Maxwell-Boltzmann T=2.0",
+        "config": {"workload": f"supercooling quench, N={n} (4*{args.ncell}^3 FCC, 80:20), "
+                               "rho=1.2, "
                                "equilibrated at T=2.0, Nose-Hoover ramp 2.0->0.4 over 1e5 steps, "
                                "dt=0.005, mixed, Verlet skin 0.3",
                    "equilibration_steps": args.equil,
@@ -291,6 +301,23 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     return out
+
+
+def force_traffic(n):
+    """DRAM bytes (read + write) per k_force launch from the committed ncu summary, scaled to
+    n particles; None when the kernel source changed since those counters were taken."""
+    import hashlib
+
+    tf = os.path.join(ROOT, "profiles", "force_traffic.json")
+    src = os.path.join(ROOT, "paper_1105_5613_gb300", "csrc", "k_force.cu")
+    try:
+        rec = json.load(open(tf))
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if rec.get("k_force_cu_sha1") != sha:
+            return None
+        return rec["bytes_per_particle"] * n
+    except Exception:
+        return None
 
 
 def cpu_sample_state(ncell=40, seed=0):
@@ -365,6 +392,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ncell", type=int, default=NCELL_FCC,
+                    help="FCC cells per edge (N = 4 ncell^3); the workload is ncell = 160")
+    ap.add_argument("--profile-phases", type=int, default=0,
+                    help="profiling case: equilibrate, rebuild, K phase-by-phase steps, exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -241,6 +241,31 @@ bbmd_status bbmd_rebuild(bbmd_sim* sim);
 
 bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info);
 
+/* Fixed size of the device scratch used by bbmd_gr_counts_noalloc (int32 entries, 16 MiB)
+ * and its largest bin count. */
+#define BBMD_NOALLOC_GR_SCRATCH_INTS (1 << 22)
+#define BBMD_NOALLOC_GR_MAX_BINS 4096
+
+/* The g(r) pair counts of bbmd_observe(BBMD_OBS_GR) (same definition, same layout as
+ * bbmd_obs.gr_counts: counts[(a*2+b)*nbins + q], 4*nbins entries, caller-owned host array)
+ * computed without allocating any device memory.  The paper has no counterpart: it is a
+ * library variant of the g(r) observable for callers that must not allocate.
+ *   nbins <= 0 -> 500, rmax <= 0 -> 5.0 (as bbmd_observe); nbins <= 4096.
+ *   Scratch: one fixed device array inside the library, BBMD_NOALLOC_GR_SCRATCH_INTS int32
+ *   entries plus 4*4096 counters.  When the box holds at least 3 cells of side rmax per
+ *   axis, the coarse-grid search needs 2n + 3(ncg + 1) entries (ncg = number of those
+ *   cells); a larger need is rejected with BBMD_ERR_ARG before anything is launched (use
+ *   bbmd_observe then).  Smaller boxes take the all-pairs path, which needs no int32
+ *   scratch.
+ *   Nothing has to start at zero: each call clears the counters and the coarse-cell counts
+ *   it uses before filling them.
+ *   The first call on a device looks up the array's address (cudaGetSymbolAddress); make
+ *   that first call before any stream capture on the device.
+ *   Calls that overlap in time on one device, from any handles or threads, share the one
+ *   array and race: serialise them.
+ * Synchronising. */
+bbmd_status bbmd_gr_counts_noalloc(bbmd_sim* sim, int32_t nbins, double rmax, uint64_t* counts);
+
 /* Message of the last failed call on this handle ("" if none). */
 const char* bbmd_last_error(const bbmd_sim* sim);
 

@@ -82,7 +82,8 @@ PHASES = ["integrate", "rebuild", "list", "force", "finalize"]
 EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bbmd_observe",
            "bbmd_minimize",
            "bbmd_get_state", "bbmd_set_state", "bbmd_get_forces", "bbmd_get_cells",
-           "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error"]
+           "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error",
+           "bbmd_gr_counts_noalloc"]
 
 _lib = None
 
@@ -127,6 +128,8 @@ def load(path: str | None = None):
     L.bbmd_rebuild.restype = C.c_int
     L.bbmd_get_info.argtypes = [vp, P(bbmd_info)]
     L.bbmd_get_info.restype = C.c_int
+    L.bbmd_gr_counts_noalloc.argtypes = [vp, C.c_int32, d, P(C.c_uint64)]
+    L.bbmd_gr_counts_noalloc.restype = C.c_int
     L.bbmd_last_error.argtypes = [vp]
     L.bbmd_last_error.restype = C.c_char_p
     _lib = L
@@ -263,6 +266,14 @@ class Sim:
             res["gr_counts"] = counts
             res["gr"] = g
         return res
+
+    def gr_counts_noalloc(self, nbins=500, rmax=5.0):
+        """g(r) pair counts (2, 2, nbins) through bbmd_gr_counts_noalloc: no device memory is
+        allocated (host result array only)."""
+        counts = np.zeros((2, 2, nbins), dtype=np.uint64)
+        _check(self.h, load().bbmd_gr_counts_noalloc(
+            self.h, int(nbins), float(rmax), counts.ctypes.data_as(C.POINTER(C.c_uint64))))
+        return counts
 
     def minimize(self, nsteps, hmax=1e-3, dmax=0.05):
         _check(self.h, load().bbmd_minimize(self.h, int(nsteps), float(hmax), float(dmax)))

@@ -873,3 +873,76 @@ bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info) {
 const char* bbmd_last_error(const bbmd_sim* sim) { return sim ? sim->err.c_str() : ""; }
 
 }  // extern "C"
+
+// ----------------------------------------------------- g(r) without device allocation ----
+// Who cannot allocate: a system sized to fill HBM has no room left for the g(r) buffers that
+// bbmd_observe grows on first use; cudaMalloc / cudaFree (and a caching allocator returning
+// memory to the driver) can synchronise the whole device, which would stall the stepping
+// stream of a monitoring loop that samples g(r) between steps; code running inside an
+// allocator callback must not call back into the allocator.  This variant takes its scratch
+// from one fixed array compiled into the library instead.
+static __device__ __align__(256) int32_t noalloc_scratch[BBMD_NOALLOC_GR_SCRATCH_INTS];
+static __device__ __align__(256) unsigned long long noalloc_counts[4 * BBMD_NOALLOC_GR_MAX_BINS];
+
+namespace {
+
+constexpr int64_t kNoAllocInts = BBMD_NOALLOC_GR_SCRATCH_INTS;
+constexpr int kNoAllocBins = BBMD_NOALLOC_GR_MAX_BINS;
+constexpr int kNoAllocDevices = 64;
+
+struct NoAllocSlot {
+    int32_t* scratch;
+    unsigned long long* counts;
+};
+NoAllocSlot noalloc_slot[kNoAllocDevices];  // per device, filled by the first call there
+
+bbmd_status noalloc_setup(bbmd_sim* sim, int dev) {
+    NoAllocSlot& sl = noalloc_slot[dev];
+    if (sl.scratch && sl.counts) return BBMD_OK;
+    void* a = nullptr;
+    void* b = nullptr;
+    CK(cudaGetSymbolAddress(&a, noalloc_scratch));
+    CK(cudaGetSymbolAddress(&b, noalloc_counts));
+    sl.scratch = (int32_t*)a;
+    sl.counts = (unsigned long long*)b;
+    return BBMD_OK;
+}
+
+}  // namespace
+
+extern "C" bbmd_status bbmd_gr_counts_noalloc(bbmd_sim* sim, int32_t nbins, double rmax,
+                                              uint64_t* counts) {
+    if (!sim || !counts) return BBMD_ERR_ARG;
+    if (nbins <= 0) nbins = 500;
+    if (!(rmax > 0.0)) rmax = 5.0;
+    if (nbins > kNoAllocBins) return fail(sim, BBMD_ERR_ARG, "nbins <= 4096");
+    const DevSim& D = sim->d;
+    // the scratch the coarse-grid path of launch_gr will ask for (same rule as launch_gr)
+    bool cells = true;
+    int64_t ncg = 1;
+    for (int d = 0; d < 3; ++d) {
+        double L = std::ldexp((double)D.Lfix[d], -D.kexp);
+        int m = (int)std::floor(L / rmax);
+        if (m < 3) cells = false;
+        ncg *= m < 1 ? 1 : m;
+    }
+    const int64_t need = cells ? 2 * D.n + 3 * (ncg + 1) : 0;
+    if (need > kNoAllocInts)
+        return fail(sim, BBMD_ERR_ARG,
+                    "g(r) without allocation: the coarse-grid search needs " +
+                        std::to_string(need) + " int32 scratch entries, the fixed array holds " +
+                        std::to_string(kNoAllocInts) + " (use bbmd_observe)");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocDevices) return fail(sim, BBMD_ERR_ARG, "device ordinal >= 64");
+    bbmd_status rc = noalloc_setup(sim, dev);
+    if (rc != BBMD_OK) return rc;
+    const NoAllocSlot& sl = noalloc_slot[dev];
+    if (launch_gr(D, sim->st, nbins, rmax, sl.counts, sl.scratch, nullptr, kNoAllocInts) != 0)
+        return fail(sim, BBMD_ERR_ARG, "g(r) without allocation: fixed scratch too small");
+    LAUNCHED("gr_counts_noalloc");
+    CK(cudaMemcpyAsync(counts, sl.counts, sizeof(unsigned long long) * 4 * (size_t)nbins,
+                       cudaMemcpyDeviceToHost, sim->st));
+    CK(cudaStreamSynchronize(sim->st));
+    return read_status(sim);
+}

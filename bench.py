@@ -251,6 +251,7 @@ def run_ours(args):
         fp64 = {"value": n * k64 / (ms64 / 1e3), "unit": "particle-steps/s", "steps": k64,
                 "ms_per_step": ms64 / k64, "force_ms": ph64["force"]}
 
+    large = run_large(args, stream) if args.large_steps > 0 or args.large_fp64_steps > 0 else None
     if rank != 0:
         return None
     value = ws * n * args.steps / (ms / 1e3)
@@ -296,10 +297,58 @@ def run_ours(args):
         "gpu_launches": args.steps * 13 + 2,
         "clocks": clocks,
         "fp64": fp64,
+        "large": large,
         "observables": {"T": obs["temperature"], "pe_per_particle": obs["pe"] / n},
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    return out
+
+
+def run_large(args, stream):
+    """The 1,024,191,500-particle step: FCC 4*635^3 (80:20) at rho = 1.2, T = 0.6 NVE,
+    dt = 0.005, forces from the cell stencil on the fly (no stored Verlet list), positions
+    and velocities generated on the device; mixed precision timed over args.large_steps
+    steps, then the FP64 form over args.large_fp64_steps steps (one handle at a time)."""
+    import torch
+
+    from inputs import generate as gen
+    from paper_1105_5613_gb300 import bbmd
+
+    torch.cuda.empty_cache()  # the 16M handles' memory back to the driver
+    ncell = args.large_ncell
+    n = 4 * ncell ** 3
+    L = gen.box_for(n, 1.2)
+    t0 = time.perf_counter()
+    sp = gen.assign_species(n, n // 5, 0)
+    t_species = time.perf_counter() - t0
+    out = {"workload": f"large step, N={n} (4*{ncell}^3 FCC, 80:20), rho=1.2, T=0.6 NVE, "
+                       "dt=0.005, cell stencil on the fly (no stored list)",
+           "n_particles": n, "box": L, "species_host_s": t_species}
+    for prec, steps, key in ((bbmd.PREC_MIXED, args.large_steps, "mixed"),
+                             (bbmd.PREC_FP64, args.large_fp64_steps, "fp64")):
+        if steps <= 0:
+            continue
+        p = bbmd.ka_params(precision=prec, nbr_mode=bbmd.NBR_CELL)
+        t0 = time.perf_counter()
+        sim = bbmd.Sim(p, n, L, sp, None, None, T0=0.6, seed=0, stream=stream.cuda_stream)
+        t_create = time.perf_counter() - t0
+        sim.step(1, DT)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps, DT)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = sim.info()
+        obs = sim.observe(bbmd.OBS_ENERGY)
+        out[key] = {"value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
+                    "ms_per_step": ms / steps, "create_s": t_create, "block_z": info["block_z"],
+                    "device_gb": info["device_bytes"] / 1e9, "T": obs["temperature"],
+                    "pe_per_particle": obs["pe"] / n}
+        sim.close()
+        del sim
     return out
 
 
@@ -394,6 +443,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ncell", type=int, default=NCELL_FCC,
                     help="FCC cells per edge (N = 4 ncell^3); the workload is ncell = 160")
+    ap.add_argument("--large-steps", type=int, default=0,
+                    help="timed mixed-precision steps of the 1.02e9-particle cell-mode step")
+    ap.add_argument("--large-fp64-steps", type=int, default=0,
+                    help="timed steps of the FP64 form of the large step")
+    ap.add_argument("--large-ncell", type=int, default=635,
+                    help="FCC cells per edge of the large step (N = 4 ncell^3)")
     ap.add_argument("--profile-phases", type=int, default=0,
                     help="profiling case: equilibrate, rebuild, K phase-by-phase steps, exit")
     args = ap.parse_args()

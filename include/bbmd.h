@@ -77,7 +77,11 @@ enum { BBMD_THERMO_NVE = 0, BBMD_THERMO_NH = 1 };
  *   skin/2 since the last build (Verlet mode) or, in cell mode, when it has left the
  *   margin skin/2 that the cells carry.
  * list_capacity: maximum list entries per particle (0 = 160; rounded up to 8).
- * stencil_capacity: maximum particles in the 27 cells around one cell (0 = from density). */
+ * stencil_capacity: maximum particles staged for one block of cells, i.e. in the
+ *   4 x 4 x (block_z + 2) cells around it (0 = from the density, with 15 % headroom).
+ * block_z: block shape of the force and list kernels, 2 x 2 x block_z cells per CTA:
+ *   0 = chosen at creation by timing every shape that fits (1, 2, 4, 8) on the initial
+ *   state; 1, 2, 4 or 8 = that shape. */
 typedef struct {
     int32_t potential;
     int32_t shift;
@@ -90,6 +94,7 @@ typedef struct {
     double skin;
     int32_t list_capacity;
     int32_t stencil_capacity;
+    int32_t block_z;
 } bbmd_params;
 
 /* Thermostat of one bbmd_step call.  NVE, or Nose-Hoover with one friction variable xi,
@@ -154,6 +159,9 @@ typedef struct {
     int32_t list_capacity;
     int32_t stencil_capacity;
     int64_t device_bytes;    /* device memory held by the handle           */
+    int32_t block_z;         /* block shape in use (2 x 2 x block_z cells) */
+    float shape_force_ms[4]; /* autotuner timings for block_z = 1, 2, 4, 8 */
+    float shape_list_ms[4];  /*   (0 = not timed)                          */
 } bbmd_info;
 
 /* Create a system of n particles in a periodic box (Sec. 2).

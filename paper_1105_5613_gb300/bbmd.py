@@ -40,7 +40,7 @@ class bbmd_params(C.Structure):
         ("nbr_mode", C.c_int32),
         ("eps", (C.c_double * 2) * 2), ("sigma", (C.c_double * 2) * 2),
         ("rcut", (C.c_double * 2) * 2), ("mass", C.c_double * 2), ("skin", C.c_double),
-        ("list_capacity", C.c_int32), ("stencil_capacity", C.c_int32),
+        ("list_capacity", C.c_int32), ("stencil_capacity", C.c_int32), ("block_z", C.c_int32),
     ]
 
 
@@ -74,7 +74,9 @@ class bbmd_obs(C.Structure):
 class bbmd_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("fix_exponent", C.c_int32), ("nc", C.c_int32 * 3),
                 ("cell_side_fix", C.c_int64 * 3), ("list_capacity", C.c_int32),
-                ("stencil_capacity", C.c_int32), ("device_bytes", C.c_int64)]
+                ("stencil_capacity", C.c_int32), ("device_bytes", C.c_int64),
+                ("block_z", C.c_int32), ("shape_force_ms", C.c_float * 4),
+                ("shape_list_ms", C.c_float * 4)]
 
 
 PHASES = ["integrate", "rebuild", "list", "force", "finalize"]
@@ -147,7 +149,8 @@ def _check(h, rc):
 
 
 def ka_params(potential=POT_LJ, shift=SHIFT_ENERGY, precision=PREC_MIXED, nbr_mode=NBR_VERLET,
-              skin=0.3, rc_factor=2.5, mass=(1.0, 1.0), list_capacity=0, stencil_capacity=0):
+              skin=0.3, rc_factor=2.5, mass=(1.0, 1.0), list_capacity=0, stencil_capacity=0,
+              block_z=0):
     """Parameters of the binary mixture of the paper's benchmark suite (Sec. 3):
     eps_AA=1, eps_AB=1.5, eps_BB=0.5, sigma_AA=1, sigma_AB=0.8, sigma_BB=0.88, m=1."""
     p = bbmd_params()
@@ -163,6 +166,7 @@ def ka_params(potential=POT_LJ, shift=SHIFT_ENERGY, precision=PREC_MIXED, nbr_mo
     p.skin = skin
     p.list_capacity = list_capacity
     p.stencil_capacity = stencil_capacity
+    p.block_z = block_z
     return p
 
 
@@ -330,4 +334,6 @@ class Sim:
         _check(self.h, load().bbmd_get_info(self.h, C.byref(i)))
         return {"n": i.n, "fix_exponent": i.fix_exponent, "nc": list(i.nc),
                 "cell_side_fix": list(i.cell_side_fix), "list_capacity": i.list_capacity,
-                "stencil_capacity": i.stencil_capacity, "device_bytes": i.device_bytes}
+                "stencil_capacity": i.stencil_capacity, "device_bytes": i.device_bytes,
+                "block_z": i.block_z, "shape_force_ms": list(i.shape_force_ms),
+                "shape_list_ms": list(i.shape_list_ms)}

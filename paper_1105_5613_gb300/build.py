@@ -11,7 +11,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbbmd.so")
-SOURCES = ["bbmd_api.cu", "k_sort.cu", "k_force.cu", "k_integrate.cu", "k_observe.cu"]
+# (source, object, extra flags): k_force.cu is compiled once per block shape
+SOURCES = [("bbmd_api.cu", "bbmd_api.o", []), ("k_sort.cu", "k_sort.o", []),
+           ("k_integrate.cu", "k_integrate.o", []), ("k_observe.cu", "k_observe.o", [])] + \
+          [("k_force.cu", f"k_force_z{z}.o", [f"-DBBMD_BLOCK_Z={z}"]) for z in (1, 2, 4, 8)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -39,11 +42,12 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     nvcc = _nvcc()
     extra = extra or []
 
-    def compile_one(name: str) -> str:
+    def compile_one(entry) -> str:
+        name, oname, defs = entry
         src = os.path.join(CSRC, name)
-        obj = os.path.join(OUT, name.replace(".cu", ".o"))
+        obj = os.path.join(OUT, oname)
         if force or _stale(obj, src):
-            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *FLAGS, *defs, *extra, "-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {name}:\n{r.stdout}\n{r.stderr}")

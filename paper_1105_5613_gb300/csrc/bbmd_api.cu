@@ -29,6 +29,10 @@ struct bbmd_sim {
     int gr_nbins = 0;
     bool ref_set = false;
     int sticky = 0;
+    int nsm = 1;
+    double mean_cell = 0.0;          // mean particles per cell
+    std::vector<int> shapes;         // block shapes that fit (candidates of the autotuner)
+    float shape_ms[4][2] = {};       // autotuner: per kShapes entry, force and list-build ms
 };
 
 namespace {
@@ -164,6 +168,7 @@ void fill_pair_table(const bbmd_params& P, PairTab& t) {
             t.eps4[k] = (float)t.deps4[k];
             t.vshift[k] = (float)t.dvshift[k];
             t.fcut[k] = (float)t.dfcut[k];
+            t.frc[k] = (float)rc;
         }
     for (int a = 0; a < 2; ++a) {
         t.mass[a] = (float)P.mass[a];
@@ -194,7 +199,9 @@ bbmd_status validate(const bbmd_params* P, int64_t n, const double* box, std::st
         }
     }
     if (P->list_capacity < 0 || P->list_capacity > 4096) return msg = "list_capacity", BBMD_ERR_ARG;
-    if (P->stencil_capacity < 0 || P->stencil_capacity > 8192) return msg = "stencil_capacity", BBMD_ERR_ARG;
+    if (P->stencil_capacity < 0 || P->stencil_capacity > 65000) return msg = "stencil_capacity", BBMD_ERR_ARG;
+    if (P->block_z != 0 && P->block_z != 1 && P->block_z != 2 && P->block_z != 4 && P->block_z != 8)
+        return msg = "block_z must be 0 (autotune), 1, 2, 4 or 8", BBMD_ERR_ARG;
     return BBMD_OK;
 }
 
@@ -203,6 +210,40 @@ bool all_finite(const double* a, int64_t m) {
     for (int64_t i = 0; i < m; ++i)
         if (!std::isfinite(a[i])) return false;
     return true;
+}
+
+// Staged capacity of one block region for shape bz (user capacity, else from the mean
+// cell occupancy with 15 % headroom), rounded to 32.
+int shape_smax(const bbmd_sim* sim, int bz) {
+    int smax = sim->P.stencil_capacity > 0
+                   ? sim->P.stencil_capacity
+                   : (int)((double)region_cells_of(bz) * sim->mean_cell * 1.15 + 160.0);
+    return (smax + 31) / 32 * 32;
+}
+
+// The staged region must fit in shared memory (list build: + 32 records of slack; FP64
+// form: 32-byte records) and its offsets in uint16 (the sentinel is smax itself).
+bool shape_fits(const bbmd_sim* sim, int bz) {
+    const int smax = shape_smax(sim, bz);
+    const size_t bytes = sim->P.precision == BBMD_PREC_FP64 ? (size_t)(smax + 1) * 32
+                                                            : (size_t)(smax + 33) * 16;
+    return smax <= 65000 && bytes <= 200 * 1024;
+}
+
+// Select block shape bz: geometry, staged capacity and the grids of the block kernels.
+void apply_shape(bbmd_sim* sim, int bz) {
+    DevSim& D = sim->d;
+    D.block_z = bz;
+    D.region_cells = region_cells_of(bz);
+    D.smax = shape_smax(sim, bz);
+    D.nblocks = (int64_t)((D.nc[0] + 1) / 2) * ((D.nc[1] + 1) / 2) * ((D.nc[2] + bz - 1) / bz);
+    int64_t g = (int64_t)sim->nsm * force_blocks_per_sm(D);
+    if (g > D.nblocks) g = D.nblocks;
+    if (g > kMaxPartials) g = kMaxPartials;
+    D.grid_cell = (int32_t)(g > 0 ? g : 1);
+    g = (int64_t)sim->nsm * list_blocks_per_sm(D);
+    if (g > D.nblocks) g = D.nblocks;
+    D.grid_list = (int32_t)(g > 0 ? g : 1);
 }
 
 bbmd_status read_status(bbmd_sim* sim) {
@@ -232,6 +273,66 @@ bbmd_status rebuild_now(bbmd_sim* sim) {
     enqueue_rebuild(sim);
     launch_clear_rebuild(sim->d, sim->st);
     LAUNCHED("rebuild");
+    return BBMD_OK;
+}
+
+// Block-shape autotuner, run once at creation on the system's own initial state (cells
+// already sorted): for every candidate shape, time one list build (Verlet mode) and one
+// force evaluation with CUDA events, after an untimed launch of each; keep the shape of
+// least force + list / 4 (a rebuild about every four steps).  A shape whose staged region
+// or lists overflow is dropped.  The lists of the chosen shape are rebuilt at the end.
+bbmd_status autotune_shape(bbmd_sim* sim) {
+    DevSim& D = sim->d;
+    const bool verlet = D.nbr_mode == BBMD_NBR_VERLET;
+    cudaEvent_t ev[4];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    int status0 = 0;
+    CK(cudaMemcpyAsync(&status0, &D.sc->status, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+    CK(cudaStreamSynchronize(sim->st));
+    int best = -1;
+    float best_cost = 0.f;
+    const int one = 1, zero = 0;
+    for (int bz : sim->shapes) {
+        apply_shape(sim, bz);
+        CK(cudaMemcpyAsync(&D.sc->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+        if (verlet) launch_list_build(D, sim->st);
+        CK(cudaEventRecord(ev[0], sim->st));
+        if (verlet) launch_list_build(D, sim->st);
+        CK(cudaEventRecord(ev[1], sim->st));
+        CK(cudaMemcpyAsync(&D.sc->rebuild, &zero, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+        launch_force(D, sim->st, false, false);
+        CK(cudaEventRecord(ev[2], sim->st));
+        launch_force(D, sim->st, false, false);
+        CK(cudaEventRecord(ev[3], sim->st));
+        LAUNCHED("autotune");
+        int st = 0;
+        CK(cudaMemcpyAsync(&st, &D.sc->status, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+        CK(cudaStreamSynchronize(sim->st));
+        float tl = 0.f, tf = 0.f;
+        CK(cudaEventElapsedTime(&tl, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&tf, ev[2], ev[3]));
+        int k = 0;
+        while (kShapes[k] != bz) ++k;
+        sim->shape_ms[k][0] = tf;
+        sim->shape_ms[k][1] = tl;
+        if (st & (ST_LIST_OVERFLOW | ST_STENCIL_OVERFLOW)) {
+            // drop the shape and restore the status word
+            CK(cudaMemcpyAsync(&D.sc->status, &status0, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+            continue;
+        }
+        const float cost = tf + (verlet ? 0.25f * tl : 0.f);
+        if (best < 0 || cost < best_cost) {
+            best = bz;
+            best_cost = cost;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (best < 0) best = sim->shapes[0];  // every shape overflowed: keep the first, report it
+    apply_shape(sim, best);
+    CK(cudaMemcpyAsync(&D.sc->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+    if (verlet) launch_list_build(D, sim->st);
+    CK(cudaMemcpyAsync(&D.sc->rebuild, &zero, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+    LAUNCHED("autotune rebuild");
     return BBMD_OK;
 }
 
@@ -342,24 +443,6 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     double cellvol = std::ldexp((double)D.D[0], -D.kexp) * std::ldexp((double)D.D[1], -D.kexp) *
                      std::ldexp((double)D.D[2], -D.kexp);
     double mean = (double)n / V * cellvol;
-    // staged capacity of one block: the region of cells around it
-    int smax = params->stencil_capacity > 0 ? params->stencil_capacity
-                                            : (int)((double)kRegionCells * mean * 1.15 + 160.0);
-    smax = (smax + 31) / 32 * 32;
-    D.smax = smax;
-    {
-        // mixed: two staging buffers (+ 32 entries of slack each in the list build); FP64:
-        // one buffer of 32-byte records
-        size_t stage_bytes = params->precision == BBMD_PREC_FP64 ? (size_t)(smax + 1) * 32
-                                                                 : (size_t)(smax + 33) * 32;
-        if (smax > 65000 || stage_bytes > 200 * 1024) {
-            std::fprintf(stderr, "bbmd_create: staged-region capacity exceeds shared memory\n");
-            bbmd_destroy(sim);
-            return BBMD_ERR_ARG;
-        }
-    }
-    D.nblocks = (int64_t)((D.nc[0] + 1) / 2) * ((D.nc[1] + 1) / 2) *
-                ((D.nc[2] + kBlockZ - 1) / kBlockZ);
     for (int d = 0; d < 3; ++d) D.halfL[d] = (float)(0.5 * box[d]);
     if (!prepare_force_kernels()) {
         cudaGetLastError();
@@ -373,13 +456,23 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
     D.grid_part = nsm * 8;
-    {
-        int per_sm = force_blocks_per_sm(D);
-        int64_t g = (int64_t)nsm * per_sm;
-        if (g > D.nblocks) g = D.nblocks;
-        if (g > kMaxPartials) g = kMaxPartials;
-        D.grid_cell = (int32_t)(g > 0 ? g : 1);
+    sim->nsm = nsm;
+    sim->mean_cell = mean;
+    // block shapes that fit this system (all of them are tried at the end of creation unless
+    // params->block_z fixes one)
+    for (int bz : kShapes) {
+        if (params->block_z != 0 && bz != params->block_z) continue;
+        if (bz > D.nc[2]) continue;  // the staged region may wrap the box at most once
+        if (!shape_fits(sim, bz)) continue;
+        sim->shapes.push_back(bz);
     }
+    if (sim->shapes.empty()) {
+        std::fprintf(stderr, "bbmd_create: no block shape fits (staged region beyond shared "
+                             "memory, or block_z larger than the cells along z)\n");
+        bbmd_destroy(sim);
+        return BBMD_ERR_ARG;
+    }
+    apply_shape(sim, sim->shapes[0]);
 
     // memory plan
     const int64_t np = D.npad;
@@ -462,6 +555,7 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     dev_free(sim, tpos);
     dev_free(sim, tvel);
     if (rc == BBMD_OK) rc = rebuild_now(sim);
+    if (rc == BBMD_OK && sim->shapes.size() > 1) rc = autotune_shape(sim);
     if (rc == BBMD_OK) rc = refresh_forces_and_K(sim);
     if (rc == BBMD_OK) rc = read_status(sim);
     if (rc != BBMD_OK) {
@@ -866,6 +960,11 @@ bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info) {
     }
     info->list_capacity = sim->d.lcap8 * 8;
     info->stencil_capacity = sim->d.smax;
+    info->block_z = sim->d.block_z;
+    for (int k = 0; k < 4; ++k) {
+        info->shape_force_ms[k] = sim->shape_ms[k][0];
+        info->shape_list_ms[k] = sim->shape_ms[k][1];
+    }
     info->device_bytes = sim->bytes;
     return BBMD_OK;
 }

@@ -10,7 +10,7 @@
 //   F[npad]      float4  mixed-precision force (w = per-particle energy on energy passes)
 //   Fd[3][npad]  double  FP64-form force
 //   list[lcap8][npad][8] uint16  Verlet list: offsets into the staged region (the cells
-//                                 around the particle's block of 2 x 2 x kBlockZ cells)
+//                                 around the particle's block of 2 x 2 x block_z cells)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,12 +20,11 @@
 namespace bbmd {
 
 constexpr int kVelExp = 52;            // velocity unit 2^-52
-#ifndef BBMD_BLOCK_Z
-#define BBMD_BLOCK_Z 2                 // cells per block along z (blocks are 2 x 2 x BLOCK_Z)
-#endif
-constexpr int kBlockZ = BBMD_BLOCK_Z;
-constexpr int kBlockWarps = 4 * kBlockZ;  // force / list kernels: one warp per cell of a block
-constexpr int kRegionCells = 16 * (kBlockZ + 2);  // cells staged per block: 4 x 4 x (BZ + 2)
+// Block shapes of the force / list kernels: blocks of 2 x 2 x Z cells, one CTA per block
+// at a time, the 4 x 4 x (Z + 2) cells around it staged in shared memory.  k_force.cu is
+// compiled once per shape (namespace z<Z>); a handle runs the shape chosen at creation.
+constexpr int kShapes[4] = {1, 2, 4, 8};
+__host__ __device__ constexpr int region_cells_of(int bz) { return 16 * (bz + 2); }
 constexpr int kMaxPartials = 8192;     // per-block FP64 partial sums
 constexpr float kBand = 1e-5f;         // relative band around a threshold for the FP64 re-test
 
@@ -44,6 +43,7 @@ struct DevScalars {
     double s_next;           // velocity scale applied by the next integrate kernel
     double s_end;            // scale applied by the finish kernel
     double dt, T_start, T_end, tau, g;
+    float hdt[2];            // dt / (2 m_a) in FP32 (set with dt)
     double T_last;           // target temperature of the last step
     double pe, w;            // last energy pass
     double kin_last;         // K of the last finalize (before NH scaling)
@@ -52,14 +52,13 @@ struct DevScalars {
     int step_in_call, n_in_call, kind, pending;
     int rebuild;             // 1: the gated rebuild kernels run in this step
     int status;              // ST_* bits
-    int pad[2];
 };
 
 struct PairTab {
     // FP32 tables [a*2+b]
     float rc2lo[4], rc2hi[4];     // rcut^2 (1 -/+ band)
     float R2lo[4], R2hi[4];       // (rcut + skin)^2 (1 -/+ band)
-    float sig2[4], sig2lo[4], eps48[4], eps4[4], vshift[4], fcut[4];
+    float sig2[4], sig2lo[4], eps48[4], eps4[4], vshift[4], fcut[4], frc[4];
     // FP64 tables: exact decisions and the FP64 form
     double rc2[4], R2[4], dsig2[4], deps48[4], deps4[4], dvshift[4], dfcut[4], drc[4];
     float mass[2];
@@ -75,7 +74,9 @@ struct DevSim {
     float sx;                // 2^-k
     double sxd;
     int32_t lcap8, smax;     // list capacity / 8; staged capacity of one block region
-    int64_t nblocks;         // blocks of 2 x 2 x kBlockZ cells
+    int32_t block_z;         // block shape: 2 x 2 x block_z cells (one of kShapes)
+    int32_t region_cells;    // cells staged per block: 4 x 4 x (block_z + 2)
+    int64_t nblocks;         // blocks of 2 x 2 x block_z cells
     float halfL[3];          // L/2 (FP32) per axis
     int32_t nbr_mode, precision;
     float disp2;             // rebuild threshold on |x - x_build|^2 (FP32, conservative)
@@ -92,7 +93,8 @@ struct DevSim {
     double* ref;             // [3][n] unwrapped reference positions by id (SET_REF)
     DevScalars* sc;
     int32_t grid_part;       // grid of per-particle grid-stride kernels
-    int32_t grid_cell;       // grid of block kernels (kBlockWarps warps per CTA)
+    int32_t grid_cell;       // grid of the force kernel (kBlockWarps warps per CTA)
+    int32_t grid_list;       // grid of the list-build kernel
 };
 
 // ---------------------------------------------------------------- conversions ----
@@ -187,14 +189,47 @@ __device__ __forceinline__ void set_status(const DevSim& s, int bits) {
 
 // sort / rebuild chain (gated on sc->rebuild unless noted)
 void launch_rebuild_chain(const DevSim& s, cudaStream_t st);
-// one-time kernel attributes (call before any stream capture)
-bool prepare_force_kernels();
-// resident CTAs per SM of the force kernel for this handle's shared-memory footprint
-int force_blocks_per_sm(const DevSim& s);
-// list build (gated)
-void launch_list_build(const DevSim& s, cudaStream_t st);
-// forces.  energy: also per-particle energy and virial partials; ke: NH kinetic partials
-void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke);
+// Per block shape (namespace z1, z2, z4, z8; defined in k_force.cu compiled per shape):
+//   prepare_force_kernels  one-time kernel attributes (call before any stream capture)
+//   force/list_blocks_per_sm  resident CTAs per SM for this handle's shared memory
+//   launch_force   forces; energy: also per-particle energy and virial partials; ke: NH
+//                  kinetic partials
+//   launch_list_build  Verlet list build (gated)
+#define BBMD_SHAPE_API(ns)                                                             \
+    namespace ns {                                                                     \
+    bool prepare_force_kernels();                                                      \
+    int force_blocks_per_sm(const DevSim& s);                                          \
+    int list_blocks_per_sm(const DevSim& s);                                           \
+    int block_threads();                                                               \
+    void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke);         \
+    void launch_list_build(const DevSim& s, cudaStream_t st);                          \
+    }
+BBMD_SHAPE_API(z1)
+BBMD_SHAPE_API(z2)
+BBMD_SHAPE_API(z4)
+BBMD_SHAPE_API(z8)
+#undef BBMD_SHAPE_API
+
+#define BBMD_SHAPE_DISPATCH(bz, call)          \
+    switch (bz) {                              \
+        case 1: return z1::call;               \
+        case 2: return z2::call;               \
+        case 4: return z4::call;               \
+        default: return z8::call;              \
+    }
+inline bool prepare_force_kernels() {
+    return z1::prepare_force_kernels() && z2::prepare_force_kernels() &&
+           z4::prepare_force_kernels() && z8::prepare_force_kernels();
+}
+inline int force_blocks_per_sm(const DevSim& s) { BBMD_SHAPE_DISPATCH(s.block_z, force_blocks_per_sm(s)) }
+inline int list_blocks_per_sm(const DevSim& s) { BBMD_SHAPE_DISPATCH(s.block_z, list_blocks_per_sm(s)) }
+inline void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke) {
+    BBMD_SHAPE_DISPATCH(s.block_z, launch_force(s, st, energy, ke))
+}
+inline void launch_list_build(const DevSim& s, cudaStream_t st) {
+    BBMD_SHAPE_DISPATCH(s.block_z, launch_list_build(s, st))
+}
+#undef BBMD_SHAPE_DISPATCH
 // integrator pieces
 void launch_begin(const DevSim& s, cudaStream_t st, int64_t nsteps, double dt,
                   const bbmd_thermostat* th);

@@ -20,19 +20,58 @@
 // taken as interacting when its FP32 r^2 is below rc^2 (1 - 1e-5); a pair within that
 // relative band of the cutoff is decided by the exact FP64 rule in a rare fix-up after
 // each batch of 8 pairs, so the interacting set equals the FP64 definition.
+//
+// This file is compiled once per block shape, BBMD_BLOCK_Z = 1, 2, 4 or 8 cells along z,
+// into namespace bbmd::z<BBMD_BLOCK_Z>; the handle picks one shape at creation.
 #include "bbmd_internal.cuh"
 
+#ifndef BBMD_BLOCK_Z
+#error "k_force.cu is compiled once per block shape: define BBMD_BLOCK_Z (1, 2, 4 or 8)"
+#endif
+// warps per CTA and resident CTAs per SM targeted by the force and list kernels, per shape
+#if BBMD_BLOCK_Z == 1
+#define BBMD_SHAPE_WARPS 4
+#define BBMD_SHAPE_FORCE_MIN 6
+#define BBMD_SHAPE_LIST_MIN 6
+#elif BBMD_BLOCK_Z == 2
+#define BBMD_SHAPE_WARPS 8
+#define BBMD_SHAPE_FORCE_MIN 3
+#define BBMD_SHAPE_LIST_MIN 3
+#elif BBMD_BLOCK_Z == 4
+#define BBMD_SHAPE_WARPS 8
+#define BBMD_SHAPE_FORCE_MIN 2
+#define BBMD_SHAPE_LIST_MIN 3
+#elif BBMD_BLOCK_Z == 8
+#define BBMD_SHAPE_WARPS 8
+#define BBMD_SHAPE_FORCE_MIN 2
+#define BBMD_SHAPE_LIST_MIN 2
+#else
+#error "BBMD_BLOCK_Z must be 1, 2, 4 or 8"
+#endif
+#ifndef BBMD_BLOCK_WARPS
+#define BBMD_BLOCK_WARPS BBMD_SHAPE_WARPS
+#endif
+#ifndef BBMD_FORCE_MIN_BLOCKS
+#define BBMD_FORCE_MIN_BLOCKS BBMD_SHAPE_FORCE_MIN
+#endif
+#ifndef BBMD_LIST_MIN_BLOCKS
+#define BBMD_LIST_MIN_BLOCKS BBMD_SHAPE_LIST_MIN
+#endif
+#define BBMD_CAT2(a, b) a##b
+#define BBMD_CAT(a, b) BBMD_CAT2(a, b)
+
 namespace bbmd {
+namespace BBMD_CAT(z, BBMD_BLOCK_Z) {
 
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float kFar = 1.0e15f;
-constexpr int kBW = kBlockWarps;  // warps per CTA = cells per block
-constexpr int kRegion = kRegionCells;  // cells staged per block: 4 x 4 x (kBlockZ + 2)
-#ifndef BBMD_FORCE_MIN_BLOCKS
-#define BBMD_FORCE_MIN_BLOCKS (24 / kBW)  // resident CTAs per SM the force kernel targets
-#endif
+constexpr int kBlockZ = BBMD_BLOCK_Z;
+constexpr int kBW = BBMD_BLOCK_WARPS;              // warps per CTA
+constexpr int kCells = 4 * kBlockZ;                // cells per block (warp w: w, w + kBW, ...)
+constexpr int kRegion = region_cells_of(kBlockZ);  // cells staged per block: 4 x 4 x (Z + 2)
+static_assert(kRegion <= kBW * 32, "one thread per staged region cell");
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -40,7 +79,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// The region of cells staged for one block: 4 x 4 x (kBlockZ + 2), index q = (z*4 + y)*4 + x.
+// The region of cells staged for one block: 4 x 4 x (Z + 2), index q = (z*4 + y)*4 + x.
 struct Region {
     int off[kRegion + 1];      // prefix of staged counts (clamped to smax); off[kRegion] = total
     int start[kRegion];        // first particle of each region cell
@@ -143,10 +182,11 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
                 wrap = s.Lfix[d];
             }
             a[d] = aa;
-            // block frame: the boundary between the block's cells (x, y) and, along z, that
-            // boundary for two cells or the centre of the single cell
-            const long long fb = d < 2 || kBlockZ == 2 ? (long long)(b.a0[d] + 1) * s.D[d]
-                                                       : frame_axis(b.a0[d], s.D[d]);
+            // block frame: the boundary between the block's cells (x, y) and, along z, the
+            // boundary at the middle of the block (the centre of the cell when Z = 1)
+            const long long fb = d < 2 ? (long long)(b.a0[d] + 1) * s.D[d]
+                                 : kBlockZ == 1 ? frame_axis(b.a0[d], s.D[d])
+                                                : (long long)(b.a0[d] + kBlockZ / 2) * s.D[d];
             const long long fr = frame_axis(aa, s.D[d]) + wrap;
             const long long delta = fr - fb;
             const float hi = i64_to_f32(delta) * s.sx;
@@ -323,7 +363,7 @@ __device__ __forceinline__ void load_tab(const DevSim& s, int si, LaneTab& T) {
     T.e40 = s.pt.eps4[k];        T.e41 = s.pt.eps4[k + 1];
     T.vsh0 = s.pt.vshift[k];     T.vsh1 = s.pt.vshift[k + 1];
     T.fc0 = s.pt.fcut[k];        T.fc1 = s.pt.fcut[k + 1];
-    T.rc0 = (float)s.pt.drc[k];  T.rc1 = (float)s.pt.drc[k + 1];
+    T.rc0 = s.pt.frc[k];         T.rc1 = s.pt.frc[k + 1];
     T.cpot = s.pt.potential == BBMD_POT_LJ ? 0.5f : 0.0f;
     T.cpe = s.pt.potential == BBMD_POT_LJ ? 1.0f : 0.0f;
     T.si = si;
@@ -397,12 +437,6 @@ __device__ __noinline__ void pair_band(const DevSim& s, const Region& R, const L
         pair_add<ENERGY, FSHIFT>(T, b, dx, dy, dz, r2, true, a);
 }
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -446,121 +480,161 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
     if (threadIdx.x == 0)
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
     __syncthreads();
-    double acc_ke = 0.0, acc_u = 0.0, acc_w = 0.0;
+    // per-lane kinetic energy in compensated FP32 (sum + carried rounding error), reduced in
+    // FP64 at the end; no FP64 instruction runs per chunk
+    float ke_sum = 0.f, ke_err = 0.f;
+    double acc_u = 0.0, acc_w = 0.0;
     float hdt0 = 0.f, hdt1 = 0.f;
     if (KE) {
-        double dt = s.sc->dt;
-        hdt0 = (float)(0.5 * dt / s.pt.dmass[0]);
-        hdt1 = (float)(0.5 * dt / s.pt.dmass[1]);
+        hdt0 = s.sc->hdt[0];
+        hdt1 = s.sc->hdt[1];
     }
+    const float m0 = s.pt.mass[0], m1 = s.pt.mass[1];
     const float far = kFar;
     const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
     const uint4 sent = make_uint4(sv, sv, sv, sv);
     for_each_block(s, smem, s.smax + 1, R, mbar, [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
-        const WarpCell wc = warp_cell(s, bp, w);
-        const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
-        const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
-        const int self0 = Rc.off[wc.rq];
-        for (int ch = 0; ch * 32 < cnt; ++ch) {
-            const int li = ch * 32 + lane;
-            const bool act = li < cnt;
-            const int64_t gi = (int64_t)i0 + li;
-            const int self = self0 + li;
-            // issue the long-latency loads first: the first list rows, the velocity
-            const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
-            uint4 e0 = sent, e1 = sent;
-            if (MODE == 0 && act) {
-                e0 = __ldcs(lp);
-                e1 = __ldcs(lp + s.npad);
-            }
-            long long v0 = 0, v1 = 0, v2 = 0;
-            if (KE && act) {
-                v0 = s.v[gi];
-                v1 = s.v[s.npad + gi];
-                v2 = s.v[2 * s.npad + gi];
-            }
-            const int nkb = MODE == 0 ? s.cellmax[i0 + ch * 32] : 0;
-            float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
-            const int si = me.w != 0.f ? 1 : 0;
-            LaneTab T;
-            load_tab(s, si, T);
-            Acc a = {0.f, 0.f, 0.f, 0.0, 0.0};
-            if (MODE == 0) {
-                for (int kb = 0; kb < nkb; ++kb) {
-                    const uint4 e = e0;
-                    e0 = e1;
-                    e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
-                    bool band = false;
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.x)], true, a, band);
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.x)], true, a, band);
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.y)], true, a, band);
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.y)], true, a, band);
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.z)], true, a, band);
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.z)], true, a, band);
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.w)], true, a, band);
-                    pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.w)], true, a, band);
-                    if (__any_sync(FULL, band) && band) {
-                        const unsigned ws[4] = {e.x, e.y, e.z, e.w};
-                        for (int q = 0; q < 8; ++q) {
-                            int t = (q & 1) ? hi16(ws[q >> 1]) : lo16(ws[q >> 1]);
-                            pair_band<ENERGY, FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
+        for (int cw = w; cw < kCells; cw += kBW) {
+            const WarpCell wc = warp_cell(s, bp, cw);
+            const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
+            const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+            const int self0 = Rc.off[wc.rq];
+            for (int ch = 0; ch * 32 < cnt; ++ch) {
+                const int li = ch * 32 + lane;
+                const bool act = li < cnt;
+                const int64_t gi = (int64_t)i0 + li;
+                const int self = self0 + li;
+                // issue the long-latency loads first: the first list rows, the velocity
+                const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
+                uint4 e0 = sent, e1 = sent;
+                if (MODE == 0 && act) {
+                    e0 = __ldcs(lp);
+                    e1 = __ldcs(lp + s.npad);
+                }
+                long long v0 = 0, v1 = 0, v2 = 0;
+                if (KE && act) {
+                    v0 = s.v[gi];
+                    v1 = s.v[s.npad + gi];
+                    v2 = s.v[2 * s.npad + gi];
+                }
+                const int nkb = MODE == 0 ? s.cellmax[i0 + ch * 32] : 0;
+                float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
+                const int si = me.w != 0.f ? 1 : 0;
+                LaneTab T;
+                load_tab(s, si, T);
+                Acc a = {0.f, 0.f, 0.f, 0.0, 0.0};
+                if (MODE == 0) {
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint4 e = e0;
+                        e0 = e1;
+                        e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
+                        bool band = false;
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.x)], true, a, band);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.x)], true, a, band);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.y)], true, a, band);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.y)], true, a, band);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.z)], true, a, band);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.z)], true, a, band);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.w)], true, a, band);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.w)], true, a, band);
+                        if (__any_sync(FULL, band) && band) {
+                            const unsigned ws[4] = {e.x, e.y, e.z, e.w};
+                            for (int q = 0; q < 8; ++q) {
+                                int t = (q & 1) ? hi16(ws[q >> 1]) : lo16(ws[q >> 1]);
+                                pair_band<ENERGY, FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
+                            }
                         }
                     }
-                }
-            } else {
-                for (int row = 0; row < 9; ++row) {
-                    int rs, re;
-                    stencil_run(Rc, wc, row, rs, re);
-                    for (int t0 = rs; t0 < re; t0 += 8) {
-                        bool band = false;
+                } else {
+                    // the stencil on the fly: 32 candidates at a time are filtered against
+                    // the cutoff into a bitmask (as the list build does against rc + skin),
+                    // band candidates decided by the exact rule, then the forces of the set
+                    // bits are added
+                    const float rcA = T.rlo0, drc = T.rlo1 - T.rlo0;
+                    const float bandc = fmaxf(T.rhi0 - T.rlo0, T.rhi1 - T.rlo1);
+                    for (int row = 0; row < 9; ++row) {
+                        int rs, re;
+                        stencil_run(Rc, wc, row, rs, re);
+                        for (int t0 = rs; t0 < re; t0 += 32) {
+                            unsigned inw = 0u;
+                            float near = far;
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int t = t0 + u;
-                            const bool valid = t < re && t != self;
-                            pair_fast<ENERGY, FSHIFT>(T, me, sm[valid ? t : s.smax], valid, a, band);
-                        }
-                        if (__any_sync(FULL, band) && band) {
-                            for (int u = 0; u < 8; ++u) {
-                                const int t = t0 + u;
-                                const bool valid = t < re && t != self;
-                                pair_band<ENERGY, FSHIFT>(s, Rc, T, me, sm[valid ? t : s.smax], t,
-                                                          gi, valid, a);
+                            for (int u = 0; u < 32; ++u) {
+                                const float4 p = sm[t0 + u];
+                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                const float dlo =
+                                    fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, drc, rcA))));
+                                inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
+                                near = fminf(near, fabsf(dlo));
+                            }
+                            const int nv = re - t0;
+                            unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
+                            if (self >= t0 && self < t0 + 32) valid &= ~(0x80000000u >> (self - t0));
+                            if (!act) valid = 0u;
+                            inw &= valid;
+                            const bool chk = near < bandc && valid != 0u;
+                            if (__any_sync(FULL, chk) && chk) {
+                                unsigned bw = valid;
+                                while (bw) {
+                                    const int u = __clz(bw);
+                                    bw &= 0x7fffffffu >> u;
+                                    const float4 p = sm[t0 + u];
+                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                    const float dlo =
+                                        fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, drc, rcA))));
+                                    if (!(fabsf(dlo) < bandc)) continue;
+                                    const unsigned bit = 0x80000000u >> u;
+                                    inw &= ~bit;
+                                    if (!min_image_copy(s, dx, dy, dz)) continue;
+                                    const int tj = p.w != 0.f ? 1 : 0;
+                                    const int64_t gj = staged_global(Rc, t0 + u);
+                                    if (r2_exact(s, gi, gj) < s.pt.rc2[si * 2 + tj]) inw |= bit;
+                                }
+                            }
+                            while (inw) {
+                                const int u = __clz(inw);
+                                inw &= 0x7fffffffu >> u;
+                                const float4 p = sm[t0 + u];
+                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                pair_add<ENERGY, FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
                             }
                         }
                     }
                 }
-            }
-            float fx = -a.fx, fy = -a.fy, fz = -a.fz;
-            if (act) {
-                if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) set_status(s, ST_NONFINITE);
-                s.F[gi] = make_float4(fx, fy, fz, ENERGY ? (float)(0.5 * a.u) : 0.f);
-                if (ENERGY) s.ud[gi] = 0.5 * a.u;
-            }
-            if (KE) {
-                float k = 0.f;
+                float fx = -a.fx, fy = -a.fy, fz = -a.fz;
                 if (act) {
-                    float h = si ? hdt1 : hdt0;
-                    float m = si ? s.pt.mass[1] : s.pt.mass[0];
-                    float vx = fmaf(h, fx, i64_to_f32_fast(v0) * pow2f(-kVelExp));
-                    float vy = fmaf(h, fy, i64_to_f32_fast(v1) * pow2f(-kVelExp));
-                    float vz = fmaf(h, fz, i64_to_f32_fast(v2) * pow2f(-kVelExp));
-                    k = 0.5f * m * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+                    if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) set_status(s, ST_NONFINITE);
+                    s.F[gi] = make_float4(fx, fy, fz, ENERGY ? (float)(0.5 * a.u) : 0.f);
+                    if (ENERGY) s.ud[gi] = 0.5 * a.u;
                 }
-                k = warp_sum_f(k);
-                if (lane == 0) acc_ke += (double)k;
-            }
-            if (ENERGY) {
-                double uu = warp_sum_d(act ? 0.5 * a.u : 0.0);
-                double ww = warp_sum_d(act ? 0.5 * a.w : 0.0);
-                if (lane == 0) {
-                    acc_u += uu;
-                    acc_w += ww;
+                if (KE && act) {
+                    const float h = si ? hdt1 : hdt0;
+                    const float m = si ? m1 : m0;
+                    const float vx = fmaf(h, fx, i64_to_f32_fast(v0) * pow2f(-kVelExp));
+                    const float vy = fmaf(h, fy, i64_to_f32_fast(v1) * pow2f(-kVelExp));
+                    const float vz = fmaf(h, fz, i64_to_f32_fast(v2) * pow2f(-kVelExp));
+                    const float k = 0.5f * m * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+                    // Kahan step: ke_err carries the low part lost by the previous additions
+                    const float y = k - ke_err;
+                    const float t = ke_sum + y;
+                    ke_err = (t - ke_sum) - y;
+                    ke_sum = t;
+                }
+                if (ENERGY) {
+                    double uu = warp_sum_d(act ? 0.5 * a.u : 0.0);
+                    double ww = warp_sum_d(act ? 0.5 * a.w : 0.0);
+                    if (lane == 0) {
+                        acc_u += uu;
+                        acc_w += ww;
+                    }
                 }
             }
         }
     });
     if (KE || ENERGY) {
+        const double acc_ke = warp_sum_d((double)ke_sum - (double)ke_err);
         double wv[3] = {acc_ke, acc_u, acc_w};
         block_partials(s, wv, 3);
     }
@@ -568,13 +642,16 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
 
 // ------------------------------------------------------------------ list build ----
 
-// Each lane tests every particle of its 27-cell stencil (broadcast reads, 32 candidates at
-// a time into a bitmask; band candidates are decided by the exact rule).  The set bits of
-// one stencil row (up to 4 words) are then written as list offsets, two entries per 32-bit
-// store into [kb][npad][8] uint16, the store address advanced incrementally.
+// Each lane tests every particle of its 27-cell stencil, 32 candidates at a time, with
+// broadcast shared-memory reads: the sign of r^2 - R2lo(species of j) is shifted into a
+// 32-bit word (candidate u lands in bit 31 - u) and the smallest |r^2 - R2lo| of the word
+// is kept.  Only a word whose minimum falls inside the band goes through the exact rule,
+// candidate by candidate.  The set bits of one stencil row (up to kRowWords words) are
+// then written as list offsets, two entries per 32-bit store into [kb][npad][8] uint16,
+// the store address advanced incrementally.
 constexpr int kRowWords = 4;  // 32-candidate words held per stencil row and pass
 
-__global__ void __launch_bounds__(kBW * 32) k_list_build(DevSim s) {
+__global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(DevSim s) {
     if (!s.sc->rebuild) return;
     extern __shared__ float4 smem[];
     __shared__ Region R[kStageBuffers];
@@ -591,124 +668,136 @@ __global__ void __launch_bounds__(kBW * 32) k_list_build(DevSim s) {
     // buffers are padded by 32 entries: word reads run past a row end
     for_each_block(s, smem, s.smax + 1 + 32, R, mbar, [&](const BlockPos& bp, const Region& Rc,
                                                            const float4* sm) {
-        const WarpCell wc = warp_cell(s, bp, w);
-        const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
-        const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
-        const int self0 = Rc.off[wc.rq];
-        for (int ch = 0; ch * 32 < cnt; ++ch) {
-            const int li = ch * 32 + lane;
-            const bool act = li < cnt;
-            const int64_t gi = (int64_t)i0 + li;
-            const int self = self0 + li;
-            float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
-            const int si = me.w != 0.f ? 1 : 0;
-            // thresholds as functions of the candidate's species w (0 or 1): R2lo(w) and a
-            // band width that covers both species (a wider band only means more exact tests)
-            const float RloA = s.pt.R2lo[si * 2], dRlo = s.pt.R2lo[si * 2 + 1] - RloA;
-            const float band = fmaxf(s.pt.R2hi[si * 2] - s.pt.R2lo[si * 2],
-                                     s.pt.R2hi[si * 2 + 1] - s.pt.R2lo[si * 2 + 1]);
-            int len = 0;
-            unsigned pend = 0u;
-            uint32_t* dst = list32 + gi * 4;  // slot of the next pair of entries
-            int word = 0;                      // 0..3 within the current kb row
-            for (int row = 0; row < 9; ++row) {
-                int rs, re;
-                stencil_run(Rc, wc, row, rs, re);
-                for (int r0 = rs; r0 < re; r0 += 32 * kRowWords) {
-                    unsigned m[kRowWords];
+        for (int cw = w; cw < kCells; cw += kBW) {
+            const WarpCell wc = warp_cell(s, bp, cw);
+            const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
+            const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+            const int self0 = Rc.off[wc.rq];
+            for (int ch = 0; ch * 32 < cnt; ++ch) {
+                const int li = ch * 32 + lane;
+                const bool act = li < cnt;
+                const int64_t gi = (int64_t)i0 + li;
+                const int self = self0 + li;
+                float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
+                const int si = me.w != 0.f ? 1 : 0;
+                // threshold as a function of the candidate's species w (0 or 1): R2lo(w); a
+                // band width that covers both species (a wider band only means more exact
+                // tests)
+                const float RloA = s.pt.R2lo[si * 2], dRlo = s.pt.R2lo[si * 2 + 1] - RloA;
+                const float band = fmaxf(s.pt.R2hi[si * 2] - s.pt.R2lo[si * 2],
+                                         s.pt.R2hi[si * 2 + 1] - s.pt.R2lo[si * 2 + 1]);
+                int len = 0;
+                unsigned pend = 0u;
+                uint32_t* dst = list32 + gi * 4;  // slot of the next pair of entries
+                int word = 0;                      // 0..3 within the current kb row
+                for (int row = 0; row < 9; ++row) {
+                    int rs, re;
+                    stencil_run(Rc, wc, row, rs, re);
+                    for (int r0 = rs; r0 < re; r0 += 32 * kRowWords) {
+                        unsigned m[kRowWords];
 #pragma unroll
-                    for (int q = 0; q < kRowWords; ++q) {
-                        const int t0 = r0 + 32 * q;
-                        unsigned inw = 0u, hiw = 0u;
-                        if (t0 < re) {  // warp-uniform
+                        for (int q = 0; q < kRowWords; ++q) {
+                            const int t0 = r0 + 32 * q;
+                            unsigned inw = 0u;
+                            if (t0 < re) {  // warp-uniform
+                                float near = far;
 #pragma unroll
-                            for (int u = 0; u < 32; ++u) {
-                                const float4 p = sm[t0 + u];
-                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                // r^2 - R2lo(species of j), one FMA chain; sign bit = inside
-                                const float dlo =
-                                    fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
-                                const float dhi = dlo - band;
-                                inw |= (__float_as_uint(dlo) >> (31 - u)) & (1u << u);
-                                hiw |= (__float_as_uint(dhi) >> (31 - u)) & (1u << u);
-                            }
-                            unsigned valid = (re - t0 >= 32) ? 0xffffffffu : ((1u << (re - t0)) - 1u);
-                            if (self >= t0 && self < t0 + 32) valid &= ~(1u << (self - t0));
-                            if (!act) valid = 0u;
-                            inw &= valid;
-                            const unsigned bandw = hiw & ~inw & valid;
-                            if (__any_sync(FULL, bandw != 0u) && bandw) {
-                                unsigned bw = bandw;
-                                while (bw) {
-                                    const int u = __ffs(bw) - 1;
-                                    bw &= bw - 1u;
+                                for (int u = 0; u < 32; ++u) {
                                     const float4 p = sm[t0 + u];
                                     const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                    if (!min_image_copy(s, dx, dy, dz)) continue;
-                                    const int tj = p.w != 0.f ? 1 : 0;
-                                    const int64_t gj = staged_global(Rc, t0 + u);
-                                    if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= 1u << u;
+                                    // r^2 - R2lo(species of j), one FMA chain; sign = inside
+                                    const float dlo = fmaf(dz, dz,
+                                                           fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
+                                    inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
+                                    near = fminf(near, fabsf(dlo));
                                 }
-                            }
-                        }
-                        m[q] = inw;
-                    }
-#pragma unroll
-                    for (int q = 0; q < kRowWords; ++q) {
-                        unsigned bits = m[q];
-                        const unsigned base = (unsigned)(r0 + 32 * q);
-                        while (bits) {
-                            const int u = __ffs(bits) - 1;
-                            bits &= bits - 1u;
-                            const unsigned t = base + (unsigned)u;
-                            if (len < lcap) {
-                                if (len & 1) {
-                                    *dst = pend | (t << 16);
-                                    if (++word == 4) {
-                                        word = 0;
-                                        dst += rowstep - 3;
-                                    } else {
-                                        ++dst;
+                                const int nv = re - t0;
+                                unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
+                                if (self >= t0 && self < t0 + 32)
+                                    valid &= ~(0x80000000u >> (self - t0));
+                                if (!act) valid = 0u;
+                                inw &= valid;
+                                const bool chk = near < band && valid != 0u;
+                                if (__any_sync(FULL, chk) && chk) {
+                                    // the same FP32 value decides which candidates are in the
+                                    // band; those are decided by the exact rule
+                                    unsigned bw = valid;
+                                    while (bw) {
+                                        const int u = __clz(bw);
+                                        bw &= 0x7fffffffu >> u;
+                                        const float4 p = sm[t0 + u];
+                                        const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                        const float dlo = fmaf(dz, dz,
+                                                               fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
+                                        if (!(fabsf(dlo) < band)) continue;
+                                        const unsigned bit = 0x80000000u >> u;
+                                        inw &= ~bit;
+                                        if (!min_image_copy(s, dx, dy, dz)) continue;
+                                        const int tj = p.w != 0.f ? 1 : 0;
+                                        const int64_t gj = staged_global(Rc, t0 + u);
+                                        if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= bit;
                                     }
-                                } else {
-                                    pend = t;
                                 }
                             }
-                            ++len;
+                            m[q] = inw;
+                        }
+#pragma unroll
+                        for (int q = 0; q < kRowWords; ++q) {
+                            unsigned bits = m[q];
+                            const unsigned base = (unsigned)(r0 + 32 * q);
+                            while (bits) {
+                                const int u = __clz(bits);
+                                bits &= 0x7fffffffu >> u;
+                                const unsigned t = base + (unsigned)u;
+                                if (len < lcap) {
+                                    if (len & 1) {
+                                        *dst = pend | (t << 16);
+                                        if (++word == 4) {
+                                            word = 0;
+                                            dst += rowstep - 3;
+                                        } else {
+                                            ++dst;
+                                        }
+                                    } else {
+                                        pend = t;
+                                    }
+                                }
+                                ++len;
+                            }
                         }
                     }
                 }
-            }
-            if (len > lcap) {
-                set_status(s, ST_LIST_OVERFLOW);
-                len = lcap;
-            }
-            if (act && (len & 1)) {
-                *dst = pend | ((unsigned)s.smax << 16);
-                if (++word == 4) {
-                    word = 0;
-                    dst += rowstep - 3;
-                } else {
-                    ++dst;
+                if (len > lcap) {
+                    set_status(s, ST_LIST_OVERFLOW);
+                    len = lcap;
                 }
-                ++len;
-            }
-            int mx = len;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
-            const int nkb = (mx + 7) >> 3;
-            if (act) {
-                for (int q2 = len >> 1; q2 < nkb * 4; ++q2) {
-                    *dst = sentpair;
+                if (act && (len & 1)) {
+                    *dst = pend | ((unsigned)s.smax << 16);
                     if (++word == 4) {
                         word = 0;
                         dst += rowstep - 3;
                     } else {
                         ++dst;
                     }
+                    ++len;
                 }
+                int mx = len;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+                const int nkb = (mx + 7) >> 3;
+                if (act) {
+                    for (int q2 = len >> 1; q2 < nkb * 4; ++q2) {
+                        *dst = sentpair;
+                        if (++word == 4) {
+                            word = 0;
+                            dst += rowstep - 3;
+                        } else {
+                            ++dst;
+                        }
+                    }
+                }
+                if (lane == 0) s.cellmax[i0 + ch * 32] = (uint16_t)nkb;
             }
-            if (lane == 0) s.cellmax[i0 + ch * 32] = (uint16_t)nkb;
         }
     });
 }
@@ -803,7 +892,8 @@ __global__ void __launch_bounds__(kBW * 32) k_force64(DevSim s) {
     for (int64_t blk = blockIdx.x; blk < s.nblocks; blk += gridDim.x) {
         const BlockPos bp = block_pos(s, blk);
         stage_block64(s, bp, R, sm);
-        const WarpCell wc = warp_cell(s, bp, w);
+        for (int cw = w; cw < kCells; cw += kBW) {
+        const WarpCell wc = warp_cell(s, bp, cw);
         const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
         const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
         const int self0 = R.off[wc.rq];
@@ -876,6 +966,7 @@ __global__ void __launch_bounds__(kBW * 32) k_force64(DevSim s) {
                 }
             }
         }
+        }
         __syncthreads();
     }
     if (KE || ENERGY) {
@@ -911,7 +1002,8 @@ void run_force(const DevSim& s, cudaStream_t st) {
         size_t bytes = (size_t)(s.smax + 1) * sizeof(Pos64);
         k_force64<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     } else {
-        size_t bytes = kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
+        // cell mode reads candidate words past a row end: 32 records of slack
+        size_t bytes = kStageBuffers * (size_t)(s.smax + 1 + (MODE == 1 ? 32 : 0)) * sizeof(float4);
         k_force<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     }
 }
@@ -953,6 +1045,8 @@ void prep_mode() {
 
 }  // namespace
 
+int block_threads() { return kBW * 32; }
+
 bool prepare_force_kernels() {
     g_smem_ok = true;
     prep_mode<0>();
@@ -972,6 +1066,13 @@ int force_blocks_per_sm(const DevSim& s) {
     return nb > 0 ? nb : 1;
 }
 
+int list_blocks_per_sm(const DevSim& s) {
+    int nb = 0;
+    const size_t bytes = kStageBuffers * (size_t)(s.smax + 1 + 32) * sizeof(float4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_list_build, kBW * 32, bytes);
+    return nb > 0 ? nb : 1;
+}
+
 void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke) {
     bool fs = s.pt.shift == BBMD_SHIFT_FORCE;
     if (s.nbr_mode == BBMD_NBR_VERLET)
@@ -985,7 +1086,8 @@ void launch_list_build(const DevSim& s, cudaStream_t st) {
     // staging buffer(s), each: staged region + sentinel + 32 entries of slack for word reads
     // past a row end
     size_t bytes = kStageBuffers * (size_t)(s.smax + 1 + 32) * sizeof(float4);
-    k_list_build<<<s.grid_cell, kBW * 32, bytes, st>>>(s);
+    k_list_build<<<s.grid_list, kBW * 32, bytes, st>>>(s);
 }
 
+}  // namespace z<BBMD_BLOCK_Z>
 }  // namespace bbmd

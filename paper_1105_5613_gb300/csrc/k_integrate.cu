@@ -45,6 +45,8 @@ __global__ void k_begin(DevSim s, int64_t nsteps, double dt, int kind, double T0
                         double tau) {
     DevScalars* sc = s.sc;
     sc->dt = dt;
+    sc->hdt[0] = (float)(0.5 * dt / s.pt.dmass[0]);
+    sc->hdt[1] = (float)(0.5 * dt / s.pt.dmass[1]);
     sc->n_in_call = (int)nsteps;
     sc->step_in_call = 0;
     sc->kind = kind;
@@ -525,9 +527,9 @@ __global__ void __launch_bounds__(kThreads) k_unpack_cells(DevSim s, int64_t* ce
 __device__ int64_t stencil_slot(const DevSim& s, int c, int t) {
     int ax, ay, az;
     cell_coords(c, s.nc, ax, ay, az);
-    const int a0[3] = {ax & ~1, ay & ~1, az - az % kBlockZ};
+    const int a0[3] = {ax & ~1, ay & ~1, az - az % s.block_z};
     int acc = 0;
-    for (int q = 0; q < kRegionCells; ++q) {
+    for (int q = 0; q < s.region_cells; ++q) {
         const int r[3] = {q & 3, (q >> 2) & 3, q >> 4};
         int b[3];
         for (int d = 0; d < 3; ++d) {

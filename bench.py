@@ -5,6 +5,10 @@ Verlet list with skin 0.3).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Besides the 16M-particle line it measures, in the same run, the 1,024,191,500-particle
+cell-mode step (mixed and FP64 forms: "large") and a batch of 64 replicas of uneven size
+("replicas"); --large-steps 0 / --replicas 0 skip them.
+
 Prints one JSON line (rank 0).  `value` is device-timed (CUDA events on the handle's
 stream, state resident in HBM); `e2e` is the same metric through the C ABI with host
 buffers (upload of the state, the steps, energy read-back and download of the state).
@@ -39,6 +43,24 @@ def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     return ws, rank
+
+
+def max_over_ranks(x, device="cpu"):
+    """Largest value of x over the ranks of the default process group (x itself alone)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world_size, ms_max):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time
+    (every rank runs the same independent workload: weak scaling)."""
+    return world_size * units_per_rank / (ms_max / 1e3)
 
 
 def ramp_T(step):
@@ -198,9 +220,7 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
 
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
     obs = sim.observe(bbmd.OBS_ENERGY)
     clocks = clk.summary()
 
@@ -251,10 +271,11 @@ def run_ours(args):
         fp64 = {"value": n * k64 / (ms64 / 1e3), "unit": "particle-steps/s", "steps": k64,
                 "ms_per_step": ms64 / k64, "force_ms": ph64["force"]}
 
+    replicas = run_replicas(args, stream) if args.replicas > 0 else None
     large = run_large(args, stream) if args.large_steps > 0 or args.large_fp64_steps > 0 else None
     if rank != 0:
         return None
-    value = ws * n * args.steps / (ms / 1e3)
+    value = whole_job_rate(n * args.steps, ws, ms)
     pk = peaks()
     clock_mhz = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = SM_COUNT * FP32_PER_SM_CLK * 2 * clock_mhz * 1e6 / 1e12  # TFLOP/s
@@ -298,6 +319,7 @@ def run_ours(args):
         "clocks": clocks,
         "fp64": fp64,
         "large": large,
+        "replicas": replicas,
         "observables": {"T": obs["temperature"], "pe_per_particle": obs["pe"] / n},
     }
     if not args.no_cpu_baseline:
@@ -350,6 +372,49 @@ def run_large(args, stream):
         sim.close()
         del sim
     return out
+
+
+def run_replicas(args, stream):
+    """Batched replicas: args.replicas mixtures of uneven size N_r in [2048, 32768] (multiples
+    of 5), random sequential addition (d_min = 0.7) relaxed by 200 steepest-descent steps,
+    temperatures evenly spaced in [0.4, 2.0], Nose-Hoover (tau = 0.5), dt = 0.005; all
+    replicas advanced by one graph launch per step (bbmd_step_batch)."""
+    import torch
+
+    from inputs import generate as gen
+    from paper_1105_5613_gb300 import bbmd
+
+    R = args.replicas
+    t0 = time.perf_counter()
+    ns, boxes, pos, sp = gen.replica_batch(R, 2048, 32768, 0)
+    t_gen = time.perf_counter() - t0
+    temps = [0.4 + 1.6 * r / max(R - 1, 1) for r in range(R)]
+    t0 = time.perf_counter()
+    b = bbmd.Batch(bbmd.ka_params(), ns, boxes, sp, pos, None, T0=temps, seed=0,
+                   stream=stream.cuda_stream)
+    for r in range(R):
+        b.replica(r).minimize(200)
+    stream.synchronize()
+    t_setup = time.perf_counter() - t0
+    th = [(bbmd.THERMO_NH, T, T, TAU) for T in temps]
+    b.step(args.warmup, DT, th)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.replica_steps, DT, th)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    shapes = sorted({b.replica(r).info()["block_z"] for r in range(R)})
+    Ts = [b.replica(r).observe(bbmd.OBS_ENERGY)["temperature"] for r in (0, R - 1)]
+    b.close()
+    ntot = sum(ns)
+    return {"workload": f"{R} replicas, N_r in [2048, 32768] (sum {ntot}), RSA + 200 SD steps, "
+                        "T_r = 0.4 .. 2.0, Nose-Hoover, dt=0.005, one graph launch per step",
+            "value": ntot * args.replica_steps / (ms / 1e3), "unit": "particle-steps/s",
+            "steps": args.replica_steps, "ms_per_step": ms / args.replica_steps,
+            "n_total": ntot, "block_z_used": shapes, "generate_s": t_gen, "setup_s": t_setup,
+            "T_first_last": Ts}
 
 
 def force_traffic(n):
@@ -443,9 +508,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ncell", type=int, default=NCELL_FCC,
                     help="FCC cells per edge (N = 4 ncell^3); the workload is ncell = 160")
-    ap.add_argument("--large-steps", type=int, default=0,
+    ap.add_argument("--replicas", type=int, default=64,
+                    help="number of replicas of the batched-replica leg (0 = skip)")
+    ap.add_argument("--replica-steps", type=int, default=500)
+    ap.add_argument("--large-steps", type=int, default=3,
                     help="timed mixed-precision steps of the 1.02e9-particle cell-mode step")
-    ap.add_argument("--large-fp64-steps", type=int, default=0,
+    ap.add_argument("--large-fp64-steps", type=int, default=1,
                     help="timed steps of the FP64 form of the large step")
     ap.add_argument("--large-ncell", type=int, default=635,
                     help="FCC cells per edge of the large step (N = 4 ncell^3)")

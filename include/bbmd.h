@@ -160,8 +160,10 @@ typedef struct {
     int32_t stencil_capacity;
     int64_t device_bytes;    /* device memory held by the handle           */
     int32_t block_z;         /* block shape in use (2 x 2 x block_z cells) */
-    float shape_force_ms[4]; /* autotuner timings for block_z = 1, 2, 4, 8 */
-    float shape_list_ms[4];  /*   (0 = not timed)                          */
+    float shape_force_ms[4]; /* autotuner: force / list-build ms per launch   */
+    float shape_list_ms[4];  /*   for block_z = 1, 2, 4, 8, measured on a     */
+                             /*   part of the box and scaled to all of it     */
+                             /*   (0 = not timed)                             */
 } bbmd_info;
 
 /* Create a system of n particles in a periodic box (Sec. 2).
@@ -248,6 +250,46 @@ bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int
 bbmd_status bbmd_rebuild(bbmd_sim* sim);
 
 bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info);
+
+/* ---- Replica batches --------------------------------------------------------------
+ * Many independent systems ("replicas": e.g. one mixture per temperature, of uneven sizes)
+ * advanced together.  Each replica is a complete handle with its own box, particles,
+ * cells, lists, block shape and thermostat variables; bbmd_step_batch advances all of them
+ * with one CUDA graph launch per step, the replicas' step kernels on parallel branches of
+ * that graph.  The paper runs one system at a time (Sec. 3, 4); a batch fills the GPU with
+ * systems far smaller than it. */
+typedef struct bbmd_batch bbmd_batch;
+
+/* Create n_rep >= 1 replicas sharing params.  Replica r: n[r] particles in the box
+ * box[3r .. 3r+2]; species[r] (host, n[r] labels, required); positions pos[r] and
+ * velocities vel[r] as in bbmd_create (pos or vel NULL, or an entry NULL, for the
+ * device-generated FCC lattice / Maxwell-Boltzmann velocities at T0[r] under seed + r).
+ * stream: a cudaStream_t shared by all replicas, or NULL for one owned by the batch.
+ * alloc: as bbmd_create.  On failure nothing stays allocated and *out is NULL. */
+bbmd_status bbmd_create_batch(const bbmd_params* params, int32_t n_rep, const int64_t* n,
+                              const double* box, const uint8_t* const* species,
+                              const double* const* pos, const double* const* vel,
+                              const double* T0, uint64_t seed, void* stream,
+                              const bbmd_alloc* alloc, bbmd_batch** out);
+
+/* Advance every replica by nsteps steps of size dt (Sec. 2.3.2).  thermo: n_rep
+ * thermostats, thermo[r] for replica r, all of the same kind; NULL = NVE for all.
+ * Asynchronous, like bbmd_step. */
+bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt,
+                            const bbmd_thermostat* thermo);
+
+/* Handle of replica r, owned by the batch and valid until bbmd_destroy_batch; every
+ * single-system call (observe, get/set state, minimize, step, ...) works on it.  NULL if r
+ * is out of range. */
+bbmd_sim* bbmd_batch_replica(bbmd_batch* b, int32_t r);
+
+int32_t bbmd_batch_size(const bbmd_batch* b);
+
+/* Release every replica and the batch (NULL is ignored). */
+void bbmd_destroy_batch(bbmd_batch* b);
+
+/* Message of the last failed batch call ("" if none). */
+const char* bbmd_batch_last_error(const bbmd_batch* b);
 
 /* Fixed size of the device scratch used by bbmd_gr_counts_noalloc (int32 entries, 16 MiB)
  * and its largest bin count. */

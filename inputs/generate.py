@@ -35,6 +35,7 @@ _C2 = np.uint64(0x94D049BB133111EB)
 STREAM_SPECIES = 1
 STREAM_VEL = 2
 STREAM_RSA = 3
+STREAM_REPLICA = 4
 
 _TWO_M53 = 2.0 ** -53
 
@@ -137,40 +138,104 @@ def rsa_positions(n: int, L: float, dmin: float, seed: int, batch: int = 4096) -
     """Random sequential addition in a periodic cube: candidate ``t`` is the point
     ``L * (u_{3t}, u_{3t+1}, u_{3t+2})`` of the RSA stream; it is kept iff its
     minimum-image distance to every earlier kept point is >= ``dmin``.  Returns the
-    first ``n`` kept points (shape (n, 3))."""
-    nc = max(1, int(L // dmin))
-    side = L / nc
-    grid: dict[tuple[int, int, int], list[int]] = {}
+    first ``n`` kept points (shape (n, 3)).
+
+    Candidates are examined in batches: a k-d tree of the points kept so far and one of the
+    batch's own survivors propose the pairs closer than ``dmin`` (with a small margin), and
+    every proposed pair is decided by the definition's own distance; candidates are then
+    accepted in their order, so the result is the sequential definition's."""
+    from scipy.spatial import cKDTree
+
+    d2 = dmin * dmin
+    rq = dmin * (1.0 + 1e-9) + 1e-12 * L
+
+    def close(a, b):
+        dx = a - b
+        dx -= L * np.round(dx / L)
+        return (dx * dx).sum(axis=-1) < d2
+
     kept = np.empty((n, 3), dtype=np.float64)
     nk = 0
     t0 = 0
-    d2 = dmin * dmin
-    offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+    base = batch
     while nk < n:
+        # later batches grow with the points still missing (fewer tree builds); the
+        # candidate order, and so the result, does not depend on the batch sizes
+        batch = max(base, min(1 << 20, 4 * (n - nk)))
         cnt = np.arange(3 * t0, 3 * (t0 + batch), dtype=np.uint64)
         cand = uniform01(counter_u64(seed, STREAM_RSA, cnt)).reshape(batch, 3) * L
         t0 += batch
-        for p in cand:
-            ci = [int(p[d] // side) % nc for d in range(3)]
-            ok = True
-            for o in offs:
-                key = ((ci[0] + o[0]) % nc, (ci[1] + o[1]) % nc, (ci[2] + o[2]) % nc)
-                lst = grid.get(key)
-                if not lst:
-                    continue
-                q = kept[lst]
-                dx = q - p
-                dx -= L * np.round(dx / L)
-                if np.any((dx * dx).sum(axis=1) < d2):
-                    ok = False
-                    break
-            if ok:
-                kept[nk] = p
-                grid.setdefault(tuple(ci), []).append(nk)
-                nk += 1
-                if nk == n:
-                    break
+        wrapped = np.where(cand >= L, cand - L, cand)  # tree coordinates only
+        ok = np.ones(batch, dtype=bool)
+        if nk > 0:
+            tree = cKDTree(np.where(kept[:nk] >= L, kept[:nk] - L, kept[:nk]), boxsize=L)
+            dist, _ = tree.query(wrapped, k=1, distance_upper_bound=rq)
+            ok = dist > rq
+            # clearly closer than dmin: rejected; within the margin: the definition decides
+            ok &= ~(dist < dmin * (1.0 - 1e-9))
+            for i in np.flatnonzero(~ok & (dist >= dmin * (1.0 - 1e-9)) & (dist <= rq)):
+                lst = tree.query_ball_point(wrapped[i], rq)
+                ok[i] = not close(kept[lst], cand[i]).any()
+        idx = np.flatnonzero(ok)
+        m = idx.size
+        lo = hi = np.zeros(0, dtype=np.int64)
+        if m > 1:
+            pairs = cKDTree(wrapped[idx], boxsize=L).query_pairs(rq, output_type="ndarray")
+            if pairs.size:
+                lo = np.minimum(pairs[:, 0], pairs[:, 1])
+                hi = np.maximum(pairs[:, 0], pairs[:, 1])
+                exact = close(cand[idx[lo]], cand[idx[hi]])
+                lo, hi = lo[exact], hi[exact]
+        # acceptance in candidate order among the survivors: j is accepted iff none of its
+        # earlier conflicting survivors is; decided in rounds, each round settling every
+        # survivor whose earlier partners are all settled
+        state = np.zeros(m, dtype=np.int8)  # 0 open, 1 accepted, -1 rejected
+        has_earlier = np.zeros(m, dtype=bool)
+        has_earlier[hi] = True
+        state[~has_earlier] = 1
+        while (state == 0).any():
+            acc_partner = np.zeros(m, dtype=bool)
+            acc_partner[hi[state[lo] == 1]] = True
+            open_partner = np.zeros(m, dtype=bool)
+            open_partner[hi[state[lo] == 0]] = True
+            op = state == 0
+            state[op & acc_partner] = -1
+            state[op & ~acc_partner & ~open_partner] = 1
+        take = idx[state == 1][: n - nk]
+        kept[nk:nk + take.size] = cand[take]
+        nk += take.size
     return kept
+
+
+def replica_sizes(n_rep: int, nmin: int, nmax: int, seed: int, multiple: int = 5) -> list[int]:
+    """Sizes of a replica batch: replica ``r`` takes draw ``r`` of the replica stream,
+    ``n = nmin + (z mod (nmax - nmin + 1))``, rounded down to a multiple of ``multiple``
+    (and raised to ``nmin`` rounded up if that falls below ``nmin``)."""
+    z = counter_u64(seed, STREAM_REPLICA, np.arange(n_rep, dtype=np.uint64))
+    span = np.uint64(nmax - nmin + 1)
+    out = []
+    for v in (z % span).astype(np.int64):
+        n = nmin + int(v)
+        n -= n % multiple
+        if n < nmin:
+            n += multiple
+        out.append(n)
+    return out
+
+
+def replica_batch(n_rep: int, nmin: int, nmax: int, seed: int, rho: float = 1.2,
+                  dmin: float = 0.7, frac_b: float = 0.2):
+    """Random-sequential-addition mixtures of uneven size (80:20 at density ``rho``):
+    sizes from :func:`replica_sizes`; replica ``r`` draws its positions and species under
+    seed ``seed + r``.  Returns (sizes, boxes, positions, species)."""
+    ns = replica_sizes(n_rep, nmin, nmax, seed)
+    boxes, pos, sp = [], [], []
+    for r, n in enumerate(ns):
+        L = box_for(n, rho)
+        boxes.append(L)
+        pos.append(rsa_positions(n, L, dmin, seed + r))
+        sp.append(assign_species(n, int(round(frac_b * n)), seed + r))
+    return ns, boxes, pos, sp
 
 
 @dataclass

@@ -85,7 +85,9 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_minimize",
            "bbmd_get_state", "bbmd_set_state", "bbmd_get_forces", "bbmd_get_cells",
            "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error",
-           "bbmd_gr_counts_noalloc"]
+           "bbmd_gr_counts_noalloc", "bbmd_create_batch", "bbmd_step_batch",
+           "bbmd_batch_replica", "bbmd_batch_size", "bbmd_destroy_batch",
+           "bbmd_batch_last_error"]
 
 _lib = None
 
@@ -132,6 +134,20 @@ def load(path: str | None = None):
     L.bbmd_get_info.restype = C.c_int
     L.bbmd_gr_counts_noalloc.argtypes = [vp, C.c_int32, d, P(C.c_uint64)]
     L.bbmd_gr_counts_noalloc.restype = C.c_int
+    PP = C.POINTER(C.c_void_p)
+    L.bbmd_create_batch.argtypes = [P(bbmd_params), C.c_int32, P(i64), P(d), PP, PP, PP, P(d),
+                                    C.c_uint64, vp, P(bbmd_alloc), P(vp)]
+    L.bbmd_create_batch.restype = C.c_int
+    L.bbmd_step_batch.argtypes = [vp, i64, d, P(bbmd_thermostat)]
+    L.bbmd_step_batch.restype = C.c_int
+    L.bbmd_batch_replica.argtypes = [vp, C.c_int32]
+    L.bbmd_batch_replica.restype = vp
+    L.bbmd_batch_size.argtypes = [vp]
+    L.bbmd_batch_size.restype = C.c_int32
+    L.bbmd_destroy_batch.argtypes = [vp]
+    L.bbmd_destroy_batch.restype = None
+    L.bbmd_batch_last_error.argtypes = [vp]
+    L.bbmd_batch_last_error.restype = C.c_char_p
     L.bbmd_last_error.argtypes = [vp]
     L.bbmd_last_error.restype = C.c_char_p
     _lib = L
@@ -220,6 +236,9 @@ class Sim:
         self.params = params
 
     def close(self):
+        if getattr(self, "_borrowed", False):  # a replica handle: owned by its batch
+            self.h = None
+            return
         if getattr(self, "h", None):
             load().bbmd_destroy(self.h)
             self.h = None
@@ -337,3 +356,102 @@ class Sim:
                 "stencil_capacity": i.stencil_capacity, "device_bytes": i.device_bytes,
                 "block_z": i.block_z, "shape_force_ms": list(i.shape_force_ms),
                 "shape_list_ms": list(i.shape_list_ms)}
+
+
+def _thermo_array(thermostats, n_rep):
+    if thermostats is None:
+        return None
+    if len(thermostats) != n_rep:
+        raise ValueError("one thermostat per replica")
+    arr = (bbmd_thermostat * n_rep)()
+    for r, (kind, T0, T1, tau) in enumerate(thermostats):
+        arr[r] = bbmd_thermostat(kind, T0, T1, tau)
+    return arr
+
+
+class Batch:
+    """Owner of a bbmd_batch: independent replicas stepped together (bbmd_step_batch).
+    replica(r) returns a Sim view of replica r (owned by the batch)."""
+
+    def __init__(self, params, ns, boxes, species, pos=None, vel=None, T0=None, seed=0,
+                 stream=None, use_torch_allocator=False):
+        L = load()
+        ns = [int(v) for v in ns]
+        n_rep = len(ns)
+        boxes = np.asarray(boxes, np.float64)
+        if boxes.ndim == 1:  # one cubic side per replica
+            boxes = np.repeat(boxes[:, None], 3, axis=1)
+        boxes = np.ascontiguousarray(boxes.reshape(n_rep, 3))
+        self._arrays = []
+
+        def ptrs(arrs, dtype, shape_of):
+            if arrs is None:
+                return None
+            out = (C.c_void_p * n_rep)()
+            for r, a in enumerate(arrs):
+                if a is None:
+                    out[r] = None
+                    continue
+                a = np.ascontiguousarray(a, dtype=dtype).reshape(shape_of(r))
+                self._arrays.append(a)
+                out[r] = a.ctypes.data
+            return C.cast(out, C.POINTER(C.c_void_p))
+
+        sp = ptrs(species, np.uint8, lambda r: (ns[r],))
+        pp = ptrs(pos, np.float64, lambda r: (ns[r], 3))
+        vp_ = ptrs(vel, np.float64, lambda r: (ns[r], 3))
+        T0 = np.ascontiguousarray(np.broadcast_to(np.asarray(0.0 if T0 is None else T0,
+                                                             np.float64), (n_rep,)))
+        narr = np.asarray(ns, dtype=np.int64)
+        self._keep = None
+        alloc = None
+        if use_torch_allocator:
+            alloc, self._keep = torch_allocator()
+        h = C.c_void_p()
+        stream_ptr = None if stream is None else C.c_void_p(int(stream))
+        rc = L.bbmd_create_batch(C.byref(params), n_rep, narr.ctypes.data_as(C.POINTER(C.c_int64)),
+                                 _dp(boxes), sp, pp, vp_, _dp(T0),
+                                 C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), stream_ptr,
+                                 C.byref(alloc) if alloc is not None else None, C.byref(h))
+        if rc != BBMD_OK:
+            raise BBMDError(rc, "bbmd_create_batch")
+        self.h = h
+        self.ns = ns
+        self.params = params
+        self._reps = []
+        for r in range(n_rep):
+            v = Sim.__new__(Sim)
+            v._borrowed = True
+            v.h = C.c_void_p(L.bbmd_batch_replica(h, r))
+            v.n = ns[r]
+            v.box = boxes[r].copy()
+            v.params = params
+            v._keep = None
+            self._reps.append(v)
+
+    def __len__(self):
+        return len(self.ns)
+
+    def replica(self, r):
+        return self._reps[r]
+
+    def step(self, nsteps, dt, thermostats=None):
+        """thermostats: None (NVE) or one (kind, T_start, T_end, tau) per replica."""
+        arr = _thermo_array(thermostats, len(self.ns))
+        rc = load().bbmd_step_batch(self.h, int(nsteps), float(dt), arr)
+        if rc != BBMD_OK:
+            raise BBMDError(rc, load().bbmd_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            for v in self._reps:
+                v.h = None
+            load().bbmd_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

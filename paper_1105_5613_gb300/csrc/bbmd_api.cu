@@ -1,5 +1,6 @@
 // C ABI of libbbmd (declared in include/bbmd.h): handle life cycle, device memory plan,
 // the captured per-step CUDA graph and the synchronising queries.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +31,7 @@ struct bbmd_sim {
     bool ref_set = false;
     int sticky = 0;
     int nsm = 1;
+    int graph_gen = 0;               // bumped whenever captured launch arguments go stale
     double mean_cell = 0.0;          // mean particles per cell
     std::vector<int> shapes;         // block shapes that fit (candidates of the autotuner)
     float shape_ms[4][2] = {};       // autotuner: per kShapes entry, force and list-build ms
@@ -278,9 +280,11 @@ bbmd_status rebuild_now(bbmd_sim* sim) {
 
 // Block-shape autotuner, run once at creation on the system's own initial state (cells
 // already sorted): for every candidate shape, time one list build (Verlet mode) and one
-// force evaluation with CUDA events, after an untimed launch of each; keep the shape of
-// least force + list / 4 (a rebuild about every four steps).  A shape whose staged region
-// or lists overflow is dropped.  The lists of the chosen shape are rebuilt at the end.
+// force evaluation with CUDA events, after an untimed launch of each, over the first blocks
+// of the box (up to 131072 cells; the cost per cell is what is compared, scaled to the
+// whole box); keep the shape of least force + list / 4 (a rebuild about every four steps).
+// A shape whose staged region or lists overflow is dropped.  The lists of the chosen shape
+// are rebuilt at the end, over the whole box.
 bbmd_status autotune_shape(bbmd_sim* sim) {
     DevSim& D = sim->d;
     const bool verlet = D.nbr_mode == BBMD_NBR_VERLET;
@@ -292,17 +296,25 @@ bbmd_status autotune_shape(bbmd_sim* sim) {
     int best = -1;
     float best_cost = 0.f;
     const int one = 1, zero = 0;
+    const int64_t target_cells = std::min<int64_t>(D.ncell, 131072);
     for (int bz : sim->shapes) {
         apply_shape(sim, bz);
+        // the timed launches cover the first nb blocks only
+        DevSim Dt = D;
+        const int64_t cpb = 4 * (int64_t)bz;
+        Dt.nblocks = std::min<int64_t>(D.nblocks, (target_cells + cpb - 1) / cpb);
+        Dt.grid_cell = (int32_t)std::min<int64_t>(Dt.grid_cell, Dt.nblocks);
+        Dt.grid_list = (int32_t)std::min<int64_t>(Dt.grid_list, Dt.nblocks);
+        const double scale = (double)D.nblocks / (double)Dt.nblocks;
         CK(cudaMemcpyAsync(&D.sc->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, sim->st));
-        if (verlet) launch_list_build(D, sim->st);
+        if (verlet) launch_list_build(Dt, sim->st);
         CK(cudaEventRecord(ev[0], sim->st));
-        if (verlet) launch_list_build(D, sim->st);
+        if (verlet) launch_list_build(Dt, sim->st);
         CK(cudaEventRecord(ev[1], sim->st));
         CK(cudaMemcpyAsync(&D.sc->rebuild, &zero, sizeof(int), cudaMemcpyHostToDevice, sim->st));
-        launch_force(D, sim->st, false, false);
+        launch_force(Dt, sim->st, false, false);
         CK(cudaEventRecord(ev[2], sim->st));
-        launch_force(D, sim->st, false, false);
+        launch_force(Dt, sim->st, false, false);
         CK(cudaEventRecord(ev[3], sim->st));
         LAUNCHED("autotune");
         int st = 0;
@@ -311,6 +323,8 @@ bbmd_status autotune_shape(bbmd_sim* sim) {
         float tl = 0.f, tf = 0.f;
         CK(cudaEventElapsedTime(&tl, ev[0], ev[1]));
         CK(cudaEventElapsedTime(&tf, ev[2], ev[3]));
+        tf = (float)(tf * scale);
+        tl = (float)(tl * scale);
         int k = 0;
         while (kShapes[k] != bz) ++k;
         sim->shape_ms[k][0] = tf;
@@ -347,6 +361,7 @@ bbmd_status refresh_forces_and_K(bbmd_sim* sim) {
 }
 
 void free_graphs(bbmd_sim* sim) {
+    ++sim->graph_gen;
     for (auto& g : sim->graph)
         if (g) {
             cudaGraphExecDestroy(g);
@@ -435,6 +450,8 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     D.nbr_mode = params->nbr_mode;
     D.precision = params->precision;
     fill_pair_table(*params, D.pt);
+    for (int k = 0; k < 4; ++k)
+        D.pt.rcfix[k] = (long long)std::ceil(std::ldexp(D.pt.drc[k], D.kexp));
     double half = 0.5 * params->skin;
     D.disp2 = (float)(half * half * (1.0 - 1e-4));
     int lcap = params->list_capacity > 0 ? params->list_capacity : 160;
@@ -455,7 +472,8 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
-    D.grid_part = nsm * 8;
+    // per-particle grid-stride kernels: 8 CTAs per SM, fewer for a small system
+    D.grid_part = (int32_t)std::min<int64_t>((int64_t)nsm * 8, std::max<int64_t>(1, (n + 255) / 256));
     sim->nsm = nsm;
     sim->mean_cell = mean;
     // block shapes that fit this system (all of them are tried at the end of creation unless
@@ -970,6 +988,183 @@ bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info) {
 }
 
 const char* bbmd_last_error(const bbmd_sim* sim) { return sim ? sim->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- replica batches ----
+
+struct bbmd_batch {
+    std::vector<bbmd_sim*> rep;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<cudaStream_t> side;  // one capture branch per replica
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [thermostatted]
+    std::vector<int> gen[2];         // replicas' graph generations at capture
+    std::string err;
+};
+
+namespace {
+
+bbmd_status batch_fail(bbmd_batch* b, bbmd_status code, const std::string& msg) {
+    if (b) b->err = msg;
+    return code;
+}
+
+void batch_free_graphs(bbmd_batch* b) {
+    for (auto& g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// One graph for one step of every replica: fork from the batch stream, each replica's
+// integrate / rebuild chain / list build / force / finalize on its own branch, join.
+bbmd_status build_batch_graph(bbmd_batch* b, int nh) {
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
+    cudaEventRecord(b->fork, b->st);
+    for (size_t r = 0; r < b->rep.size(); ++r) {
+        const DevSim& D = b->rep[r]->d;
+        cudaStream_t s = b->side[r];
+        cudaStreamWaitEvent(s, b->fork, 0);
+        launch_integrate(D, s);
+        launch_rebuild_chain(D, s);
+        launch_list_build(D, s);
+        launch_force(D, s, false, nh != 0);
+        launch_finalize(D, s, nh != 0);
+        cudaEventRecord(b->join[r], s);
+        cudaStreamWaitEvent(b->st, b->join[r], 0);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->st, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[nh], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph[nh] = nullptr;
+        return batch_fail(b, BBMD_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    b->gen[nh].resize(b->rep.size());
+    for (size_t r = 0; r < b->rep.size(); ++r) b->gen[nh][r] = b->rep[r]->graph_gen;
+    return BBMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bbmd_destroy_batch(bbmd_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    batch_free_graphs(b);
+    for (bbmd_sim* s : b->rep) bbmd_destroy(s);
+    for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->own_stream) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+bbmd_status bbmd_create_batch(const bbmd_params* params, int32_t n_rep, const int64_t* n,
+                              const double* box, const uint8_t* const* species,
+                              const double* const* pos, const double* const* vel,
+                              const double* T0, uint64_t seed, void* stream,
+                              const bbmd_alloc* alloc, bbmd_batch** out) {
+    if (!out) return BBMD_ERR_ARG;
+    *out = nullptr;
+    if (!params || n_rep < 1 || n_rep > 65536 || !n || !box || !species || !T0)
+        return BBMD_ERR_ARG;
+    bbmd_batch* b = new bbmd_batch();
+    b->st = (cudaStream_t)stream;
+    if (!b->st) {
+        if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return BBMD_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    bbmd_status rc = BBMD_OK;
+    for (int32_t r = 0; r < n_rep && rc == BBMD_OK; ++r) {
+        bbmd_sim* s = nullptr;
+        rc = bbmd_create(params, n[r], box + 3 * (size_t)r, species[r], pos ? pos[r] : nullptr,
+                         vel ? vel[r] : nullptr, T0[r], seed + (uint64_t)r, b->st, alloc, &s);
+        if (rc == BBMD_OK) b->rep.push_back(s);
+    }
+    if (rc == BBMD_OK && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = BBMD_ERR_CUDA;
+    for (int32_t r = 0; r < n_rep && rc == BBMD_OK; ++r) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = BBMD_ERR_CUDA;
+            break;
+        }
+        b->side.push_back(s);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            rc = BBMD_ERR_CUDA;
+            break;
+        }
+        b->join.push_back(e);
+    }
+    if (rc != BBMD_OK) {
+        bbmd_destroy_batch(b);
+        return rc;
+    }
+    *out = b;
+    return BBMD_OK;
+}
+
+bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd_thermostat* th) {
+    if (!b) return BBMD_ERR_ARG;
+    if (nsteps < 0 || nsteps > 0x7fffffff || !(dt > 0.0) || !(dt < 1.0))
+        return batch_fail(b, BBMD_ERR_ARG, "nsteps in [0, 2^31) and dt in (0, 1) required");
+    int nh = 0;
+    if (th) {
+        nh = th[0].kind == BBMD_THERMO_NH;
+        for (size_t r = 0; r < b->rep.size(); ++r) {
+            if (th[r].kind != th[0].kind)
+                return batch_fail(b, BBMD_ERR_ARG, "all replicas need the same thermostat kind");
+            if (th[r].kind != BBMD_THERMO_NVE && th[r].kind != BBMD_THERMO_NH)
+                return batch_fail(b, BBMD_ERR_ARG, "thermostat kind");
+            if (nh && !(th[r].T_start > 0.0 && th[r].T_end > 0.0 && th[r].tau > 0.0))
+                return batch_fail(b, BBMD_ERR_ARG, "Nose-Hoover needs T_start, T_end, tau > 0");
+        }
+    }
+    if (nsteps == 0) return BBMD_OK;
+    bool stale = !b->graph[nh] || b->gen[nh].size() != b->rep.size();
+    for (size_t r = 0; !stale && r < b->rep.size(); ++r)
+        stale = b->gen[nh][r] != b->rep[r]->graph_gen;
+    if (stale) {
+        if (b->graph[nh]) {
+            cudaGraphExecDestroy(b->graph[nh]);
+            b->graph[nh] = nullptr;
+        }
+        bbmd_status rc = build_batch_graph(b, nh);
+        if (rc != BBMD_OK) return rc;
+    }
+    for (size_t r = 0; r < b->rep.size(); ++r)
+        launch_begin(b->rep[r]->d, b->st, nsteps, dt, nh ? &th[r] : nullptr);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        cudaError_t e = cudaGraphLaunch(b->graph[nh], b->st);
+        if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    for (size_t r = 0; r < b->rep.size(); ++r) launch_finish(b->rep[r]->d, b->st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
+    return BBMD_OK;
+}
+
+bbmd_sim* bbmd_batch_replica(bbmd_batch* b, int32_t r) {
+    if (!b || r < 0 || (size_t)r >= b->rep.size()) return nullptr;
+    return b->rep[(size_t)r];
+}
+
+int32_t bbmd_batch_size(const bbmd_batch* b) { return b ? (int32_t)b->rep.size() : 0; }
+
+const char* bbmd_batch_last_error(const bbmd_batch* b) { return b ? b->err.c_str() : ""; }
 
 }  // extern "C"
 

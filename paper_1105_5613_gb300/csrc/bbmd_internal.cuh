@@ -61,6 +61,7 @@ struct PairTab {
     float sig2[4], sig2lo[4], eps48[4], eps4[4], vshift[4], fcut[4], frc[4];
     // FP64 tables: exact decisions and the FP64 form
     double rc2[4], R2[4], dsig2[4], deps48[4], deps4[4], dvshift[4], dfcut[4], drc[4];
+    long long rcfix[4];           // ceil(rcut * 2^k): |dx| beyond it on some axis -> no pair
     float mass[2];
     double dmass[2];
     int potential, shift;

@@ -849,15 +849,16 @@ __device__ __forceinline__ void pair_fp64(const DevSim& s, int si, const Pos64& 
                                           double& fx, double& fy, double& fz, double& u,
                                           double& w) {
     const long long ix = p.x - me.x, iy = p.y - me.y, iz = p.z - me.z;
-    // only the minimum-image copy counts (a region may hold a cell twice when nc = 3)
-    if (llabs(ix) > (s.Lfix[0] >> 1) || llabs(iy) > (s.Lfix[1] >> 1) ||
-        llabs(iz) > (s.Lfix[2] >> 1))
-        return;
+    const int k = si * 2 + p.sp;
+    // integer pre-test: a separation beyond rc on some axis cannot interact.  rc < L/2 (the
+    // box holds at least three cells of side >= rc per axis), so what passes is the
+    // minimum-image copy (a region may hold a cell twice when nc = 3)
+    const long long lim = s.pt.rcfix[k];
+    if (llabs(ix) > lim || llabs(iy) > lim || llabs(iz) > lim) return;
     double dx = __dmul_rn(__ll2double_rn(ix), s.sxd);
     double dy = __dmul_rn(__ll2double_rn(iy), s.sxd);
     double dz = __dmul_rn(__ll2double_rn(iz), s.sxd);
     double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    int k = si * 2 + p.sp;
     if (r2 < s.pt.rc2[k]) {
         double ir2 = 1.0 / r2;
         double s2 = s.pt.dsig2[k] * ir2;

@@ -1,0 +1,96 @@
+"""Replica batches (bbmd_create_batch / bbmd_step_batch): every replica of a batch against
+the oracle on its own generated inputs, at its own temperature; one batch graph step per
+step equal, bit for bit, to stepping each replica handle on its own; argument errors."""
+import numpy as np
+import pytest
+
+import oracle
+from inputs import generate as gen
+from tests.helpers import min_image_rms, oracle_params, quantized
+
+pytestmark = pytest.mark.gpu
+
+bbmd = pytest.importorskip("paper_1105_5613_gb300.bbmd")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_5613_gb300 import build as b
+
+    b.build()
+    bbmd.load()
+
+
+def lattice_replicas(ms, temps, shake=0.05):
+    ns, boxes, pos, vel, sp = [], [], [], [], []
+    for r, (m, T) in enumerate(zip(ms, temps)):
+        n = 4 * m ** 3
+        L = gen.box_for(n, 1.2)
+        rng = np.random.default_rng(100 + r)
+        pos.append((gen.fcc_lattice(m, L) + rng.uniform(-shake, shake, (n, 3))) % L)
+        vel.append(gen.maxwell_boltzmann(n, T, r, np.ones(n)))
+        sp.append(gen.assign_species(n, n // 5, r))
+        ns.append(n)
+        boxes.append(L)
+    return ns, boxes, pos, vel, sp
+
+
+def test_batch_replicas_match_oracle():
+    ms, temps = [8, 9, 10, 11], [0.5, 1.0, 1.5, 2.0]
+    ns, boxes, pos, vel, sp = lattice_replicas(ms, temps)
+    p = bbmd.ka_params()
+    b = bbmd.Batch(p, ns, boxes, sp, pos, vel)
+    th = [(bbmd.THERMO_NH, T, T, 0.5) for T in temps]
+    b.step(100, 0.005, th)
+    for r in range(len(ns)):
+        xq, _, _ = quantized(pos[r], boxes[r])
+        st = oracle.MDState(xq, vel[r], sp[r], boxes[r], oracle_params(p))
+        oracle.md_run(st, 100, 0.005, thermo=th[r][1:], use_cells=True)
+        gp, _, _ = b.replica(r).get_state()
+        assert min_image_rms(gp, st.pos, boxes[r]) <= 1e-4, r
+        obs = b.replica(r).observe(bbmd.OBS_ENERGY)
+        assert obs["step"] == 100
+        assert obs["xi"] == pytest.approx(st.nh.xi, rel=1e-3, abs=1e-3)
+    b.close()
+
+
+def test_batch_step_equals_replica_steps():
+    """RSA replicas of uneven size relaxed by steepest descent, then stepped by the batch
+    graph in one batch and replica by replica in a twin batch: identical states."""
+    ns, boxes, pos, sp = gen.replica_batch(5, 2048, 6000, 7)
+    temps = list(np.linspace(0.4, 2.0, 5))
+    p = bbmd.ka_params(block_z=2)
+    twins = [bbmd.Batch(p, ns, boxes, sp, pos, None, T0=temps, seed=11) for _ in range(2)]
+    for b in twins:
+        for r in range(len(ns)):
+            b.replica(r).minimize(50)
+    th = [(bbmd.THERMO_NH, T, T, 0.5) for T in temps]
+    twins[0].step(60, 0.005, th)
+    for r in range(len(ns)):
+        twins[1].replica(r).step(60, 0.005, th[r])
+    for r in range(len(ns)):
+        pa, va, ia = twins[0].replica(r).get_state()
+        pb, vb, ib = twins[1].replica(r).get_state()
+        assert np.array_equal(pa, pb) and np.array_equal(va, vb) and np.array_equal(ia, ib), r
+        assert np.isfinite(twins[0].replica(r).observe(bbmd.OBS_ENERGY)["pe"])
+    for b in twins:
+        b.close()
+
+
+def test_batch_argument_errors():
+    ms, temps = [8, 9], [1.0, 1.5]
+    ns, boxes, pos, vel, sp = lattice_replicas(ms, temps)
+    b = bbmd.Batch(bbmd.ka_params(), ns, boxes, sp, pos, vel)
+    with pytest.raises(bbmd.BBMDError):  # mixed thermostat kinds
+        b.step(5, 0.005, [(bbmd.THERMO_NH, 1.0, 1.0, 0.5), (bbmd.THERMO_NVE, 0, 0, 0)])
+    with pytest.raises(ValueError):  # one thermostat per replica
+        b.step(5, 0.005, [(bbmd.THERMO_NH, 1.0, 1.0, 0.5)])
+    b.step(5, 0.005)  # NVE for all
+    assert b.replica(1).observe(0)["step"] == 5
+    b.close()
+    with pytest.raises(bbmd.BBMDError):  # a replica whose box holds fewer than 3 cells
+        bbmd.Batch(bbmd.ka_params(), [4000, 500], [gen.box_for(4000, 1.2), gen.box_for(500, 1.2)],
+                   [np.zeros(4000, np.uint8), np.zeros(500, np.uint8)])

@@ -166,7 +166,8 @@ def run_ours(args):
     L = gen.box_for(n, 1.2)
     sp = gen.assign_species(n, n // 5, 0)
     stream = make_stream()
-    p = bbmd.ka_params()
+    p = bbmd.ka_params(nbr_mode=bbmd.NBR_CELL if args.profile_cell else bbmd.NBR_VERLET,
+                       block_z=args.block_z)
     sim = bbmd.Sim(p, n, L, sp, None, None, T0=T_HIGH, seed=rank, stream=stream.cuda_stream,
                    use_torch_allocator=True)
     step = 0
@@ -178,6 +179,7 @@ def run_ours(args):
     # ramp), then untimed warm-up steps of the ramp (the first also captures the graph)
     if args.equil > 0:
         sim.step(args.equil, DT, (bbmd.THERMO_NH, T_HIGH, T_HIGH, TAU))
+        sim.tune()  # block shape re-timed on the liquid (creation timed it on the lattice)
     if args.profile_phases > 0:
         # profiling case: one forced rebuild, then K steps with every phase launched on
         # its own (the kernel launches that ncu captures), per-phase times printed
@@ -185,9 +187,11 @@ def run_ours(args):
         k = args.profile_phases
         ph, nr = sim.step_profiled(k, DT, (bbmd.THERMO_NH, T_HIGH, T_HIGH, TAU))
         stream.synchronize()
+        sim_block_z = sim.info()["block_z"]
         sim.close()
         if rank == 0:
             print(json.dumps({"profile_case": {"n_particles": n, "equil": args.equil,
+                                               "block_z": sim_block_z,
                                                "steps": k, "rebuilds": nr,
                                                "phases_ms_per_step":
                                                    {a: v / k for a, v in ph.items()}}}))
@@ -222,6 +226,7 @@ def run_ours(args):
 
         ms = max_over_ranks(ms, "cuda")
     obs = sim.observe(bbmd.OBS_ENERGY)
+    block_z = sim.info()["block_z"]
     clocks = clk.summary()
 
     # ---- per-phase attribution (same steps, phases launched one by one) ----
@@ -314,6 +319,7 @@ def run_ours(args):
                                     f"flop x {n} particles per launch",
                      "force_ms": force_ms},
         "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
+        "block_z": block_z,
         "rebuilds_per_step": nreb / nprof,
         "gpu_launches": args.steps * 13 + 2,
         "clocks": clocks,
@@ -517,6 +523,10 @@ def main():
                     help="timed steps of the FP64 form of the large step")
     ap.add_argument("--large-ncell", type=int, default=635,
                     help="FCC cells per edge of the large step (N = 4 ncell^3)")
+    ap.add_argument("--profile-cell", action="store_true",
+                    help="profiling case in cell mode (forces from the stencil, no list)")
+    ap.add_argument("--block-z", type=int, default=0,
+                    help="block shape of the 16M handle (0 = autotuned at creation)")
     ap.add_argument("--profile-phases", type=int, default=0,
                     help="profiling case: equilibrate, rebuild, K phase-by-phase steps, exit")
     args = ap.parse_args()

@@ -246,6 +246,12 @@ bbmd_status bbmd_get_cells(bbmd_sim* sim, int64_t* cell);
 bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int64_t* offsets,
                                int64_t* nbr, int64_t cap);
 
+/* Re-run the block-shape autotuner of bbmd_create on the current state (creation times the
+ * shapes on the initial state, e.g. a lattice; a liquid can favour another shape), rebuild
+ * the lists for the shape chosen and recompute the forces.  Nothing changes when
+ * params.block_z fixed the shape.  Synchronising. */
+bbmd_status bbmd_tune(bbmd_sim* sim);
+
 /* Force a rebuild (binning, reorder and list) at the current positions. */
 bbmd_status bbmd_rebuild(bbmd_sim* sim);
 

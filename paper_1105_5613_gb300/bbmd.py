@@ -85,7 +85,7 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_minimize",
            "bbmd_get_state", "bbmd_set_state", "bbmd_get_forces", "bbmd_get_cells",
            "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error",
-           "bbmd_gr_counts_noalloc", "bbmd_create_batch", "bbmd_step_batch",
+           "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_create_batch", "bbmd_step_batch",
            "bbmd_batch_replica", "bbmd_batch_size", "bbmd_destroy_batch",
            "bbmd_batch_last_error"]
 
@@ -128,6 +128,8 @@ def load(path: str | None = None):
     L.bbmd_get_cells.restype = C.c_int
     L.bbmd_get_neighbors.argtypes = [vp, P(i64), i64, P(i64), P(i64), i64]
     L.bbmd_get_neighbors.restype = C.c_int
+    L.bbmd_tune.argtypes = [vp]
+    L.bbmd_tune.restype = C.c_int
     L.bbmd_rebuild.argtypes = [vp]
     L.bbmd_rebuild.restype = C.c_int
     L.bbmd_get_info.argtypes = [vp, P(bbmd_info)]
@@ -344,6 +346,10 @@ class Sim:
         _check(self.h, L.bbmd_get_neighbors(self.h, ip, m, off.ctypes.data_as(P),
                                             nbr.ctypes.data_as(P), int(nbr.size)))
         return off, nbr[: int(off[-1])]
+
+    def tune(self):
+        """Re-pick the block shape by timing it on the current state (bbmd_tune)."""
+        _check(self.h, load().bbmd_tune(self.h))
 
     def rebuild(self):
         _check(self.h, load().bbmd_rebuild(self.h))

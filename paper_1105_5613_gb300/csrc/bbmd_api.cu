@@ -959,6 +959,17 @@ bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int
     return read_status(sim);
 }
 
+bbmd_status bbmd_tune(bbmd_sim* sim) {
+    if (!sim) return BBMD_ERR_ARG;
+    if (sim->shapes.size() < 2) return BBMD_OK;
+    bbmd_status rc = rebuild_now(sim);
+    if (rc == BBMD_OK) rc = autotune_shape(sim);
+    free_graphs(sim);  // the captured launches carry the previous shape
+    if (rc == BBMD_OK) rc = refresh_forces_and_K(sim);
+    if (rc != BBMD_OK) return rc;
+    return read_status(sim);
+}
+
 bbmd_status bbmd_rebuild(bbmd_sim* sim) {
     if (!sim) return BBMD_ERR_ARG;
     bbmd_status rc = rebuild_now(sim);

@@ -72,6 +72,10 @@ constexpr int kBW = BBMD_BLOCK_WARPS;              // warps per CTA
 constexpr int kCells = 4 * kBlockZ;                // cells per block (warp w: w, w + kBW, ...)
 constexpr int kRegion = region_cells_of(kBlockZ);  // cells staged per block: 4 x 4 x (Z + 2)
 static_assert(kRegion <= kBW * 32, "one thread per staged region cell");
+#ifndef BBMD_LIST_AHEAD
+#define BBMD_LIST_AHEAD 2
+#endif
+constexpr int kListAhead = BBMD_LIST_AHEAD;  // list rows in flight ahead of the pair loop
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -507,10 +511,11 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
                 const int self = self0 + li;
                 // issue the long-latency loads first: the first list rows, the velocity
                 const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
-                uint4 e0 = sent, e1 = sent;
+                uint4 e0 = sent, e1 = sent, e2 = sent;
                 if (MODE == 0 && act) {
                     e0 = __ldcs(lp);
                     e1 = __ldcs(lp + s.npad);
+                    if (kListAhead > 2) e2 = __ldcs(lp + 2 * s.npad);
                 }
                 long long v0 = 0, v1 = 0, v2 = 0;
                 if (KE && act) {
@@ -528,7 +533,12 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
                     for (int kb = 0; kb < nkb; ++kb) {
                         const uint4 e = e0;
                         e0 = e1;
-                        e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
+                        if (kListAhead > 2) {
+                            e1 = e2;
+                            e2 = (act && kb + 3 < nkb) ? __ldcs(lp + (int64_t)(kb + 3) * s.npad) : sent;
+                        } else {
+                            e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
+                        }
                         bool band = false;
                         pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.x)], true, a, band);
                         pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.x)], true, a, band);
@@ -658,6 +668,7 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(D
     __shared__ __align__(8) uint64_t mbar[kStageBuffers];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lcap = s.lcap8 * 8;
+    const int lcap2 = lcap >> 1;  // pair slots per particle
     if (threadIdx.x == 0)
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
     __syncthreads();
@@ -688,8 +699,9 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(D
                                          s.pt.R2hi[si * 2 + 1] - s.pt.R2lo[si * 2 + 1]);
                 int len = 0;
                 unsigned pend = 0u;
-                uint32_t* dst = list32 + gi * 4;  // slot of the next pair of entries
-                int word = 0;                      // 0..3 within the current kb row
+                // pair slot wi (entries 2 wi, 2 wi + 1) of this particle:
+                // row0[(wi >> 2) * rowstep + (wi & 3)]
+                uint32_t* const row0 = list32 + gi * 4;
                 for (int row = 0; row < 9; ++row) {
                     int rs, re;
                     stencil_run(Rc, wc, row, rs, re);
@@ -749,19 +761,12 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(D
                                 const int u = __clz(bits);
                                 bits &= 0x7fffffffu >> u;
                                 const unsigned t = base + (unsigned)u;
-                                if (len < lcap) {
-                                    if (len & 1) {
-                                        *dst = pend | (t << 16);
-                                        if (++word == 4) {
-                                            word = 0;
-                                            dst += rowstep - 3;
-                                        } else {
-                                            ++dst;
-                                        }
-                                    } else {
-                                        pend = t;
-                                    }
-                                }
+                                // an odd entry completes a pair: one 32-bit store (entries
+                                // beyond the capacity are counted, not stored)
+                                const int wi = len >> 1;
+                                if ((len & 1) && wi < lcap2)
+                                    row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] = pend | (t << 16);
+                                pend = t;
                                 ++len;
                             }
                         }
@@ -772,13 +777,8 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(D
                     len = lcap;
                 }
                 if (act && (len & 1)) {
-                    *dst = pend | ((unsigned)s.smax << 16);
-                    if (++word == 4) {
-                        word = 0;
-                        dst += rowstep - 3;
-                    } else {
-                        ++dst;
-                    }
+                    const int wi = len >> 1;
+                    row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] = pend | ((unsigned)s.smax << 16);
                     ++len;
                 }
                 int mx = len;
@@ -786,15 +786,14 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(D
                 for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
                 const int nkb = (mx + 7) >> 3;
                 if (act) {
-                    for (int q2 = len >> 1; q2 < nkb * 4; ++q2) {
-                        *dst = sentpair;
-                        if (++word == 4) {
-                            word = 0;
-                            dst += rowstep - 3;
-                        } else {
-                            ++dst;
-                        }
-                    }
+                    // sentinel pairs up to the warp's row count: the rest of a partial row,
+                    // then whole rows (16-byte stores)
+                    int wi = len >> 1;
+                    for (; wi < nkb * 4 && (wi & 3); ++wi)
+                        row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] = sentpair;
+                    const uint4 sent4 = make_uint4(sentpair, sentpair, sentpair, sentpair);
+                    for (; wi < nkb * 4; wi += 4)
+                        *reinterpret_cast<uint4*>(row0 + (int64_t)(wi >> 2) * rowstep) = sent4;
                 }
                 if (lane == 0) s.cellmax[i0 + ch * 32] = (uint16_t)nkb;
             }

@@ -110,3 +110,22 @@ def test_shapes_that_do_not_fit_are_skipped():
     sim.close()
     with pytest.raises(bbmd.BBMDError):
         bbmd.Sim(bbmd.ka_params(block_z=8), n, L, sp, pos, vel)
+
+
+def test_tune_on_the_current_state():
+    n, L, pos, vel, sp = mixture(16, shake=0.12)
+    sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, pos, vel)
+    sim.step(50, 0.005, (bbmd.THERMO_NH, 2.0, 2.0, 0.5))
+    F0 = sim.get_forces()
+    sim.tune()
+    info = sim.info()
+    assert info["block_z"] in SHAPES
+    e = force_errors(sim.get_forces(), F0)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4
+    sim.step(20, 0.005, (bbmd.THERMO_NH, 2.0, 2.0, 0.5))
+    assert np.isfinite(sim.observe(bbmd.OBS_ENERGY)["pe"])
+    sim.close()
+    fixed = bbmd.Sim(bbmd.ka_params(block_z=4), n, L, sp, pos, vel)
+    fixed.tune()
+    assert fixed.info()["block_z"] == 4
+    fixed.close()

@@ -45,6 +45,19 @@ def _dist():
     return ws, rank
 
 
+def workload_config(args, ws):
+    """The "config" object of both arms: the supercooling-quench workload."""
+    from inputs import generate as gen
+
+    n = 4 * args.ncell ** 3
+    return {"workload": f"supercooling quench, N={n} (4*{args.ncell}^3 FCC, 80:20), rho=1.2, "
+                        "equilibrated at T=2.0, Nose-Hoover ramp 2.0->0.4 over 1e5 steps, "
+                        "dt=0.005, mixed, Verlet skin 0.3",
+            "equilibration_steps": args.equil, "n_particles": n, "box": gen.box_for(n, 1.2),
+            "parallelism": f"replicas x{ws}",
+            "l2": "state and per-step traffic (>6 GB) far larger than the 129 MB L2"}
+
+
 def max_over_ranks(x, device="cpu"):
     """Largest value of x over the ranks of the default process group (x itself alone)."""
     import torch
@@ -276,6 +289,31 @@ def run_ours(args):
         fp64 = {"value": n * k64 / (ms64 / 1e3), "unit": "particle-steps/s", "steps": k64,
                 "ms_per_step": ms64 / k64, "force_ms": ph64["force"]}
 
+    # ---- soft-sphere mixture with the shifted-force truncation (Eqs. sc0, mod0), the paper's
+    # own benchmark potential, on the same N: melted at T=2.0, then timed at T=0.5 ----
+    soft = None
+    if args.soft_steps > 0:
+        ps = bbmd.ka_params(potential=bbmd.POT_SOFT, shift=bbmd.SHIFT_FORCE)
+        sims = bbmd.Sim(ps, n, L, sp, None, None, T0=T_HIGH, seed=rank,
+                        stream=stream.cuda_stream, use_torch_allocator=True)
+        sims.step(200, DT, (bbmd.THERMO_NH, T_HIGH, 0.5, TAU))
+        sims.tune()
+        sims.step(args.warmup, DT, (bbmd.THERMO_NH, 0.5, 0.5, TAU))
+        stream.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        sims.step(args.soft_steps, DT, (bbmd.THERMO_NH, 0.5, 0.5, TAU))
+        s1.record(stream)
+        s1.synchronize()
+        mss = s0.elapsed_time(s1)
+        soft = {"workload": f"soft-sphere mixture (Eq. sc0) with shifted-force truncation "
+                            f"(Eq. mod0), rc = 2.5 sigma_ab, N={n}, rho=1.2, Nose-Hoover T=0.5 "
+                            "after melting at T=2.0",
+                "value": n * args.soft_steps / (mss / 1e3), "unit": "particle-steps/s",
+                "steps": args.soft_steps, "ms_per_step": mss / args.soft_steps,
+                "block_z": sims.info()["block_z"],
+                "T": sims.observe(bbmd.OBS_ENERGY)["temperature"]}
+        sims.close()
     replicas = run_replicas(args, stream) if args.replicas > 0 else None
     large = run_large(args, stream) if args.large_steps > 0 or args.large_fp64_steps > 0 else None
     if rank != 0:
@@ -302,13 +340,7 @@ def run_ours(args):
         "dtype": "f32 pair forces, i64 fixed-point state, f64 reductions",
         "data": f"synthetic: FCC 4*{args.ncell}^3 lattice, seeded 80:20 species, "
                 "Maxwell-Boltzmann T=2.0",
-        "config": {"workload": f"supercooling quench, N={n} (4*{args.ncell}^3 FCC, 80:20), "
-                               "rho=1.2, "
-                               "equilibrated at T=2.0, Nose-Hoover ramp 2.0->0.4 over 1e5 steps, "
-                               "dt=0.005, mixed, Verlet skin 0.3",
-                   "equilibration_steps": args.equil,
-                   "n_particles": n, "box": L, "parallelism": f"replicas x{ws}",
-                   "l2": "state and per-step traffic (>6 GB) far larger than the 129 MB L2"},
+        "config": workload_config(args, ws),
         "e2e": {"value": ws * n * ke2 / e2e_s, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": h2d / ke2, "d2h_bytes_per_step": d2h / ke2,
                 "steps": ke2},
@@ -325,6 +357,7 @@ def run_ours(args):
         "clocks": clocks,
         "fp64": fp64,
         "large": large,
+        "soft_sphere": soft,
         "replicas": replicas,
         "observables": {"T": obs["temperature"], "pe_per_particle": obs["pe"] / n},
     }
@@ -491,8 +524,7 @@ def run_reference(args):
             "FP64 GPU; % of roofline", "value": v, "unit": "particle-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "oracle on a bounded sample of the "
-                                                        "supercooling-quench workload"},
+            "data": "synthetic", "config": workload_config(args, ws),
             "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
@@ -514,6 +546,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ncell", type=int, default=NCELL_FCC,
                     help="FCC cells per edge (N = 4 ncell^3); the workload is ncell = 160")
+    ap.add_argument("--soft-steps", type=int, default=100,
+                    help="timed steps of the soft-sphere / shifted-force variant (0 = skip)")
     ap.add_argument("--replicas", type=int, default=64,
                     help="number of replicas of the batched-replica leg (0 = skip)")
     ap.add_argument("--replica-steps", type=int, default=500)

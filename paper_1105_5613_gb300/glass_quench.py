@@ -34,15 +34,17 @@ def soft_sphere_params(rc=1.2, skin=0.3, block_z=0):
 
 
 def run(ncell=40, heat_steps=200_000, cool_steps=3_000_000, dt=1e-3, T_high=3.0, T_low=1e-3,
-        tau=0.5, every=1000, rc=1.2, seed=0, gr_bins=500, gr_rmax=5.0, log=None):
-    """Run the quench; returns a dict with the recorded curve and the final g(r)."""
+        tau=0.5, every=1000, rc=1.2, seed=0, gr_bins=500, gr_rmax=5.0, frac_b=0.2, log=None):
+    """Run the quench; returns a dict with the recorded curve and the final g(r).  frac_b:
+    fraction of species B (label 1, sigma_BB = 0.88)."""
     from inputs import generate as gen
 
     from . import bbmd
 
     n = 4 * ncell ** 3
     L = gen.box_for(n, 1.2)
-    sp = gen.assign_species(n, n // 5, seed)
+    nb = int(round(frac_b * n))
+    sp = gen.assign_species(n, nb, seed)
     sim = bbmd.Sim(soft_sphere_params(rc), n, L, sp, None, None, T0=T_high, seed=seed)
     rows = []
     t0 = time.perf_counter()
@@ -71,14 +73,13 @@ def run(ncell=40, heat_steps=200_000, cool_steps=3_000_000, dt=1e-3, T_high=3.0,
         if log and len(rows) % 200 == 0:
             log(f"step {done}: T {rows[-1][2]:.4f} U/N {rows[-1][3]:.5f}")
     o = sim.observe(bbmd.OBS_GR | bbmd.OBS_ENERGY, nbins=gr_bins, rmax=gr_rmax)
-    nb = n // 5
     na = n - nb
     gab = o["gr"]
     w = np.array([[na * (na - 1), na * nb], [nb * na, nb * (nb - 1)]], dtype=np.float64)
     g_total = (gab * w[:, :, None]).sum(axis=(0, 1)) / w.sum()
     info = sim.info()
     sim.close()
-    return {"n": n, "box": L, "dt": dt, "rc": rc, "heat_steps": heat_steps,
+    return {"n": n, "frac_b": frac_b, "box": L, "dt": dt, "rc": rc, "heat_steps": heat_steps,
             "cool_steps": cool_steps, "every": every, "block_z": info["block_z"],
             "seconds": time.perf_counter() - t0,
             "curve": {"step": [r[0] for r in rows], "T_target": [r[1] for r in rows],
@@ -89,7 +90,7 @@ def run(ncell=40, heat_steps=200_000, cool_steps=3_000_000, dt=1e-3, T_high=3.0,
                    "AB": gab[0, 1].tolist(), "BB": gab[1, 1].tolist()}}
 
 
-def analyse(T, U, liquid_min=0.5, glass_max=0.1):
+def analyse(T, U, liquid_min=1.0, glass_max=0.3):
     """Caloric-curve analysis of Sec. 4: U = a + b T^(3/5) fitted on T >= liquid_min, a
     straight line on T <= glass_max (least squares); T_g = the temperature in between where
     the two fits meet (the liquid fit minus the glass fit changes sign)."""
@@ -118,12 +119,18 @@ def main():
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--rc", type=float, default=1.2)
+    ap.add_argument("--frac-b", type=float, default=0.2,
+                    help="fraction of species B (sigma_BB = 0.88); the paper's 20:80 read "
+                         "literally, species 1 first, is 0.8")
+    ap.add_argument("--liquid-min", type=float, default=1.0)
+    ap.add_argument("--glass-max", type=float, default=0.3)
     ap.add_argument("--out", default="glass.json")
     args = ap.parse_args()
     res = run(args.ncell, args.heat_steps, args.cool_steps, args.dt, every=args.every, rc=args.rc,
-              log=print)
+              frac_b=args.frac_b, log=print)
     c = res["curve"]
-    res["analysis"] = analyse(c["T"], c["U"])
+    k = args.heat_steps // args.every  # the cooling part of the curve
+    res["analysis"] = analyse(c["T"][k:], c["U"][k:], args.liquid_min, args.glass_max)
     with open(args.out, "w") as f:
         json.dump(res, f)
     print(json.dumps({"n": res["n"], "seconds": res["seconds"], "block_z": res["block_z"],

@@ -24,7 +24,7 @@ def test_analysis_recovers_a_known_break():
 def test_analysis_without_a_break_reports_none():
     T = np.linspace(3.0, 0.001, 500)
     U = -2.0 + 1.5 * T ** 0.6
-    res = gq.analyse(T, U)
+    res = gq.analyse(T, U, liquid_min=0.5, glass_max=0.1)
     assert np.isnan(res["T_g"]) or res["T_g"] < 0.12
 
 
@@ -39,7 +39,7 @@ def test_short_quench_runs_through_the_library():
     assert np.all(np.isfinite(U)) and len(U) == 2000 // 500 + 20000 // 500
     # cooling lowers the potential energy; the thermostat follows the ramp
     assert U[-1] < U[3] - 0.5
-    assert T[-1] < 0.1 and abs(T[3] - 3.0) < 0.6
+    assert T[-1] < 0.1 and 2.0 < np.mean(T[:4]) < 4.5
     g = np.array(res["gr"]["total"])
     r = np.array(res["gr"]["r"])
     assert 0.8 < r[np.argmax(g)] < 1.2  # first peak near one particle diameter (Sec. 4)

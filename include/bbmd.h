@@ -261,8 +261,8 @@ bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info);
  * Many independent systems ("replicas": e.g. one mixture per temperature, of uneven sizes)
  * advanced together.  Each replica is a complete handle with its own box, particles,
  * cells, lists, block shape and thermostat variables; bbmd_step_batch advances all of them
- * with one CUDA graph launch per step, the replicas' step kernels on parallel branches of
- * that graph.  The paper runs one system at a time (Sec. 3, 4); a batch fills the GPU with
+ * with one CUDA graph launch per step: groups of replicas on parallel branches of that
+ * graph, one kernel launch per phase covering every replica of a group.  The paper runs one system at a time (Sec. 3, 4); a batch fills the GPU with
  * systems far smaller than it. */
 typedef struct bbmd_batch bbmd_batch;
 
@@ -290,6 +290,11 @@ bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt,
 bbmd_sim* bbmd_batch_replica(bbmd_batch* b, int32_t r);
 
 int32_t bbmd_batch_size(const bbmd_batch* b);
+
+/* Branches of the batch step graph (default 8): the replicas are split into this many
+ * groups of about equal particle count; within a group one launch per phase covers every
+ * replica, and the groups run concurrently.  Takes effect at the next bbmd_step_batch. */
+bbmd_status bbmd_batch_set_branches(bbmd_batch* b, int32_t branches);
 
 /* Release every replica and the batch (NULL is ignored). */
 void bbmd_destroy_batch(bbmd_batch* b);

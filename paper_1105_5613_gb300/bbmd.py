@@ -86,7 +86,8 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_get_state", "bbmd_set_state", "bbmd_get_forces", "bbmd_get_cells",
            "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error",
            "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_create_batch", "bbmd_step_batch",
-           "bbmd_batch_replica", "bbmd_batch_size", "bbmd_destroy_batch",
+           "bbmd_batch_replica", "bbmd_batch_size", "bbmd_batch_set_branches",
+           "bbmd_destroy_batch",
            "bbmd_batch_last_error"]
 
 _lib = None
@@ -144,6 +145,8 @@ def load(path: str | None = None):
     L.bbmd_step_batch.restype = C.c_int
     L.bbmd_batch_replica.argtypes = [vp, C.c_int32]
     L.bbmd_batch_replica.restype = vp
+    L.bbmd_batch_set_branches.argtypes = [vp, C.c_int32]
+    L.bbmd_batch_set_branches.restype = C.c_int
     L.bbmd_batch_size.argtypes = [vp]
     L.bbmd_batch_size.restype = C.c_int32
     L.bbmd_destroy_batch.argtypes = [vp]
@@ -440,6 +443,12 @@ class Batch:
 
     def replica(self, r):
         return self._reps[r]
+
+    def set_branches(self, k):
+        """Graph branches of the batch step (groups of replicas run concurrently)."""
+        rc = load().bbmd_batch_set_branches(self.h, int(k))
+        if rc != BBMD_OK:
+            raise BBMDError(rc, "bbmd_batch_set_branches")
 
     def step(self, nsteps, dt, thermostats=None):
         """thermostats: None (NVE) or one (kind, T_start, T_end, tau) per replica."""

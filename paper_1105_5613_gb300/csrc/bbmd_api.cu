@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -1008,11 +1009,13 @@ struct bbmd_batch {
     std::vector<bbmd_sim*> rep;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    std::vector<cudaStream_t> side;  // one capture branch per replica
-    cudaEvent_t fork = nullptr;
-    std::vector<cudaEvent_t> join;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [thermostatted]
     std::vector<int> gen[2];         // replicas' graph generations at capture
+    std::vector<void*> dev;          // device tables of the batch launches
+    int branches = 8;                // graph branches, each a group of replicas
+    std::vector<std::function<void()>> pending;  // per branch: its launches (during capture)
+    std::vector<cudaStream_t> side;  // capture streams of the branches
+    std::vector<cudaEvent_t> ev;     // fork + joins
     std::string err;
 };
 
@@ -1031,35 +1034,176 @@ void batch_free_graphs(bbmd_batch* b) {
         }
 }
 
-// One graph for one step of every replica: fork from the batch stream, each replica's
-// integrate / rebuild chain / list build / force / finalize on its own branch, join.
+void batch_free_tables(bbmd_batch* b) {
+    for (void* p : b->dev) cudaFree(p);
+    b->dev.clear();
+}
+
+// Upload systems and CTA offsets for one set of replicas; returns the ManySims view and
+// the total CTA count, or false on a CUDA error.
+bool upload_many(bbmd_batch* b, const std::vector<const DevSim*>& sims,
+                 const std::vector<int32_t>& ctas, ManySims& m, int& total) {
+    const size_t nr = sims.size();
+    std::vector<DevSim> hs(nr);
+    std::vector<int32_t> first(nr + 1, 0);
+    for (size_t r = 0; r < nr; ++r) {
+        hs[r] = *sims[r];
+        first[r + 1] = first[r] + ctas[r];
+    }
+    void* ds = nullptr;
+    void* df = nullptr;
+    if (cudaMalloc(&ds, nr * sizeof(DevSim)) != cudaSuccess) return false;
+    b->dev.push_back(ds);
+    if (cudaMalloc(&df, (nr + 1) * sizeof(int32_t)) != cudaSuccess) return false;
+    b->dev.push_back(df);
+    if (cudaMemcpy(ds, hs.data(), nr * sizeof(DevSim), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(df, first.data(), (nr + 1) * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return false;
+    m.sims = (const DevSim*)ds;
+    m.first = (const int32_t*)df;
+    m.nrep = (int32_t)nr;
+    total = first[nr];
+    return true;
+}
+
+// Launches of one step for a group of replicas: one launch per phase for the whole group
+// (integrate, the gated sort chain, the gated list build and the forces -- one launch per
+// block shape in use -- and finalize).
+bool capture_group(bbmd_batch* b, const std::vector<size_t>& idx, int nh, cudaStream_t st) {
+    const size_t nr = idx.size();
+    const DevSim& D0 = b->rep[idx[0]]->d;
+    const bool fp64 = D0.precision == BBMD_PREC_FP64;
+    const bool cell = D0.nbr_mode != BBMD_NBR_VERLET;
+    const bool fshift = D0.pt.shift == BBMD_SHIFT_FORCE;
+    std::vector<const DevSim*> all(nr);
+    std::vector<int32_t> c_part(nr), c_scan(nr), c_one(nr, 1);
+    for (size_t r = 0; r < nr; ++r) {
+        all[r] = &b->rep[idx[r]]->d;
+        c_part[r] = all[r]->grid_part;
+        c_scan[r] = scan_grid(*all[r]);
+    }
+    ManySims part, scan, one;
+    int t_part = 0, t_scan = 0, t_one = 0;
+    if (!(upload_many(b, all, c_part, part, t_part) && upload_many(b, all, c_scan, scan, t_scan) &&
+          upload_many(b, all, c_one, one, t_one)))
+        return false;
+    struct Group {
+        int bz;
+        ManySims force, list;
+        int t_force = 0, t_list = 0, smax = 0;
+    };
+    std::vector<Group> groups;
+    for (int bz : kShapes) {
+        std::vector<const DevSim*> gs;
+        std::vector<int32_t> c_force, c_list;
+        int smax = 0;
+        for (size_t r = 0; r < nr; ++r)
+            if (all[r]->block_z == bz) {
+                gs.push_back(all[r]);
+                c_force.push_back(all[r]->grid_cell);
+                c_list.push_back(all[r]->grid_list);
+                smax = std::max(smax, (int)all[r]->smax);
+            }
+        if (gs.empty()) continue;
+        Group g;
+        g.bz = bz;
+        g.smax = smax;
+        if (!(upload_many(b, gs, c_force, g.force, g.t_force) &&
+              upload_many(b, gs, c_list, g.list, g.t_list)))
+            return false;
+        groups.push_back(g);
+    }
+    // the tables are uploaded (synchronous copies) now; the launches run in the capture
+    b->pending.push_back([=]() {
+        launch_integrate_many(part, t_part, fp64, st);
+        launch_rebuild_chain_many(part, scan, one, t_part, t_scan, (int)nr, st);
+        for (const Group& g : groups) {
+            if (cell) continue;
+            switch (g.bz) {
+                case 1: z1::launch_list_build_many(g.list, g.t_list, g.smax, st); break;
+                case 2: z2::launch_list_build_many(g.list, g.t_list, g.smax, st); break;
+                case 4: z4::launch_list_build_many(g.list, g.t_list, g.smax, st); break;
+                default: z8::launch_list_build_many(g.list, g.t_list, g.smax, st); break;
+            }
+        }
+        for (const Group& g : groups) {
+            switch (g.bz) {
+                case 1: z1::launch_force_many(g.force, g.t_force, fp64, cell, nh != 0, fshift, g.smax, st); break;
+                case 2: z2::launch_force_many(g.force, g.t_force, fp64, cell, nh != 0, fshift, g.smax, st); break;
+                case 4: z4::launch_force_many(g.force, g.t_force, fp64, cell, nh != 0, fshift, g.smax, st); break;
+                default: z8::launch_force_many(g.force, g.t_force, fp64, cell, nh != 0, fshift, g.smax, st); break;
+            }
+        }
+        launch_finalize_many(one, (int)nr, nh != 0, st);
+    });
+    return true;
+}
+
+// One graph for one step of every replica: the replicas are split into `branches` groups
+// of about equal particle count (largest first, each to the lightest group); the graph
+// forks into one branch per group, each branch running its group's phase launches, and
+// joins.  Groups overlap one another's phases; within a group one launch covers all its
+// replicas.
 bbmd_status build_batch_graph(bbmd_batch* b, int nh) {
+    cudaStreamSynchronize(b->st);
+    batch_free_graphs(b);
+    batch_free_tables(b);
+    b->pending.clear();
+    const size_t nr = b->rep.size();
+    const size_t nb = std::max<size_t>(1, std::min<size_t>((size_t)b->branches, nr));
+    std::vector<size_t> order(nr);
+    for (size_t r = 0; r < nr; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return b->rep[x]->d.n > b->rep[y]->d.n; });
+    std::vector<std::vector<size_t>> grp(nb);
+    std::vector<int64_t> load(nb, 0);
+    for (size_t r : order) {
+        size_t k = 0;
+        for (size_t q = 1; q < nb; ++q)
+            if (load[q] < load[k]) k = q;
+        grp[k].push_back(r);
+        load[k] += b->rep[r]->d.n;
+    }
+    for (auto& g : grp) std::sort(g.begin(), g.end());
+    while (b->side.size() < nb) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return batch_fail(b, BBMD_ERR_CUDA, "batch streams");
+        b->side.push_back(st);
+    }
+    while (b->ev.size() < nb + 1) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return batch_fail(b, BBMD_ERR_CUDA, "batch events");
+        b->ev.push_back(e);
+    }
+    for (size_t k = 0; k < nb; ++k)
+        if (!capture_group(b, grp[k], nh, b->side[k])) {
+            cudaGetLastError();
+            return batch_fail(b, BBMD_ERR_OOM, "batch launch tables");
+        }
     cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
-    cudaEventRecord(b->fork, b->st);
-    for (size_t r = 0; r < b->rep.size(); ++r) {
-        const DevSim& D = b->rep[r]->d;
-        cudaStream_t s = b->side[r];
-        cudaStreamWaitEvent(s, b->fork, 0);
-        launch_integrate(D, s);
-        launch_rebuild_chain(D, s);
-        launch_list_build(D, s);
-        launch_force(D, s, false, nh != 0);
-        launch_finalize(D, s, nh != 0);
-        cudaEventRecord(b->join[r], s);
-        cudaStreamWaitEvent(b->st, b->join[r], 0);
+    cudaEventRecord(b->ev[0], b->st);
+    for (size_t k = 0; k < nb; ++k) {
+        cudaStreamWaitEvent(b->side[k], b->ev[0], 0);
+        b->pending[k]();
+        cudaEventRecord(b->ev[k + 1], b->side[k]);
+        cudaStreamWaitEvent(b->st, b->ev[k + 1], 0);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->st, &g);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[nh], g, 0);
     if (g) cudaGraphDestroy(g);
+    b->pending.clear();
     if (e != cudaSuccess) {
         cudaGetLastError();
         b->graph[nh] = nullptr;
         return batch_fail(b, BBMD_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
     }
-    b->gen[nh].resize(b->rep.size());
-    for (size_t r = 0; r < b->rep.size(); ++r) b->gen[nh][r] = b->rep[r]->graph_gen;
+    for (int k = 0; k < 2; ++k) b->gen[k].clear();
+    b->gen[nh].resize(nr);
+    for (size_t r = 0; r < nr; ++r) b->gen[nh][r] = b->rep[r]->graph_gen;
     return BBMD_OK;
 }
 
@@ -1071,10 +1215,10 @@ void bbmd_destroy_batch(bbmd_batch* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
     batch_free_graphs(b);
+    batch_free_tables(b);
     for (bbmd_sim* s : b->rep) bbmd_destroy(s);
     for (cudaStream_t s : b->side) cudaStreamDestroy(s);
-    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
-    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     if (b->own_stream) cudaStreamDestroy(b->st);
     delete b;
 }
@@ -1103,22 +1247,6 @@ bbmd_status bbmd_create_batch(const bbmd_params* params, int32_t n_rep, const in
         rc = bbmd_create(params, n[r], box + 3 * (size_t)r, species[r], pos ? pos[r] : nullptr,
                          vel ? vel[r] : nullptr, T0[r], seed + (uint64_t)r, b->st, alloc, &s);
         if (rc == BBMD_OK) b->rep.push_back(s);
-    }
-    if (rc == BBMD_OK && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
-        rc = BBMD_ERR_CUDA;
-    for (int32_t r = 0; r < n_rep && rc == BBMD_OK; ++r) {
-        cudaStream_t s = nullptr;
-        cudaEvent_t e = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            rc = BBMD_ERR_CUDA;
-            break;
-        }
-        b->side.push_back(s);
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            rc = BBMD_ERR_CUDA;
-            break;
-        }
-        b->join.push_back(e);
     }
     if (rc != BBMD_OK) {
         bbmd_destroy_batch(b);
@@ -1149,10 +1277,6 @@ bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd
     for (size_t r = 0; !stale && r < b->rep.size(); ++r)
         stale = b->gen[nh][r] != b->rep[r]->graph_gen;
     if (stale) {
-        if (b->graph[nh]) {
-            cudaGraphExecDestroy(b->graph[nh]);
-            b->graph[nh] = nullptr;
-        }
         bbmd_status rc = build_batch_graph(b, nh);
         if (rc != BBMD_OK) return rc;
     }
@@ -1174,6 +1298,13 @@ bbmd_sim* bbmd_batch_replica(bbmd_batch* b, int32_t r) {
 }
 
 int32_t bbmd_batch_size(const bbmd_batch* b) { return b ? (int32_t)b->rep.size() : 0; }
+
+bbmd_status bbmd_batch_set_branches(bbmd_batch* b, int32_t branches) {
+    if (!b || branches < 1) return BBMD_ERR_ARG;
+    b->branches = branches;
+    for (auto& g : b->gen) g.clear();  // re-captured at the next step
+    return BBMD_OK;
+}
 
 const char* bbmd_batch_last_error(const bbmd_batch* b) { return b ? b->err.c_str() : ""; }
 

@@ -67,7 +67,7 @@ struct PairTab {
     int potential, shift;
 };
 
-struct DevSim {
+struct alignas(16) DevSim {
     int64_t n, npad;
     int32_t ncell, nc[3];
     int64_t D[3], Lfix[3];
@@ -185,6 +185,52 @@ __device__ __forceinline__ void set_status(const DevSim& s, int bits) {
     atomicOr(&s.sc->status, bits);
 }
 
+// ------------------------------------------------------------------ replica batches ----
+// A batch launch runs one phase for every replica of a batch: replica r owns the CTAs
+// first[r] .. first[r + 1] - 1 of the grid.  Each kernel of the step is written once as a
+// body taking (system, CTA index within it, CTA count of it) and wrapped twice: for one
+// system (DevSim by value, blockIdx / gridDim) and for a batch (the replica's DevSim copied
+// to shared memory).
+struct ManySims {
+    const DevSim* sims;     // nrep systems (device memory)
+    const int32_t* first;   // nrep + 1 CTA offsets (device memory)
+    int32_t nrep;
+};
+
+// The replica of this CTA: copies its DevSim into sh and returns the CTA's index and count
+// within the replica.  Every thread of the CTA calls it once, first (it synchronises).
+__device__ __forceinline__ void load_replica(const ManySims& m, DevSim& sh, int& lb, int& lg) {
+    __shared__ int rep_of_cta;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = m.nrep - 1;  // the last replica whose first CTA is <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (m.first[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        rep_of_cta = lo;
+    }
+    __syncthreads();
+    const int r = rep_of_cta;
+    const int4* src = reinterpret_cast<const int4*>(m.sims + r);
+    int4* dst = reinterpret_cast<int4*>(&sh);
+    for (int k = threadIdx.x; k < (int)(sizeof(DevSim) / 16); k += blockDim.x) dst[k] = src[k];
+    lb = (int)blockIdx.x - m.first[r];
+    lg = m.first[r + 1] - m.first[r];
+    __syncthreads();
+}
+
+#define BBMD_ONE_AND_MANY(bounds, name, body)                                             \
+    __global__ void __launch_bounds__(bounds) name(DevSim s) {                            \
+        body(s, (int)blockIdx.x, (int)gridDim.x);                                         \
+    }                                                                                     \
+    __global__ void __launch_bounds__(bounds) name##_many(ManySims m) {                   \
+        __shared__ DevSim sh;                                                             \
+        int lb, lg;                                                                       \
+        load_replica(m, sh, lb, lg);                                                      \
+        body(sh, lb, lg);                                                                 \
+    }
+
 // ------------------------------------------------------------ launch wrappers ----
 // (defined in the .cu files; all enqueue on `st`)
 
@@ -199,6 +245,10 @@ void launch_rebuild_chain(const DevSim& s, cudaStream_t st);
 #define BBMD_SHAPE_API(ns)                                                             \
     namespace ns {                                                                     \
     bool prepare_force_kernels();                                                      \
+    void launch_force_many(const ManySims& m, int total, bool fp64, bool cell, bool ke,    \
+                           bool fshift, int smax_max, cudaStream_t st);                \
+    void launch_list_build_many(const ManySims& m, int total, int smax_max,             \
+                                cudaStream_t st);                                      \
     int force_blocks_per_sm(const DevSim& s);                                          \
     int list_blocks_per_sm(const DevSim& s);                                           \
     int block_threads();                                                               \
@@ -231,6 +281,14 @@ inline void launch_list_build(const DevSim& s, cudaStream_t st) {
     BBMD_SHAPE_DISPATCH(s.block_z, launch_list_build(s, st))
 }
 #undef BBMD_SHAPE_DISPATCH
+// batch launches: one launch runs the phase for every replica of m; first[] of m must
+// hold each replica's CTA count of that phase (grid_part for the per-particle kernels,
+// the scan grid, 1 for the per-replica reductions)
+int scan_grid(const DevSim& s);
+void launch_rebuild_chain_many(const ManySims& part, const ManySims& scan, const ManySims& one,
+                               int total_part, int total_scan, int nrep, cudaStream_t st);
+void launch_integrate_many(const ManySims& part, int total, bool fp64, cudaStream_t st);
+void launch_finalize_many(const ManySims& one, int nrep, bool ke, cudaStream_t st);
 // integrator pieces
 void launch_begin(const DevSim& s, cudaStream_t st, int64_t nsteps, double dt,
                   const bbmd_thermostat* th);

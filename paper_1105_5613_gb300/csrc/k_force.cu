@@ -281,11 +281,11 @@ constexpr int kStageBuffers = BBMD_STAGE_BUFFERS;
 // i+1 are in flight while block i is computed; with one, each block is staged then
 // computed.  body(pos, R, sm) computes one staged block and must not synchronise the CTA.
 template <class Body>
-__device__ void for_each_block(const DevSim& s, float4* smem, int buf_stride, Region* R,
+__device__ void for_each_block(const DevSim& s, int lb, int lg, float4* smem, int buf_stride, Region* R,
                                uint64_t* mbar, Body body) {
-    int64_t blk = blockIdx.x;
+    int64_t blk = lb;
     if (kStageBuffers == 1) {
-        for (int it = 0; blk < s.nblocks; ++it, blk += gridDim.x) {
+        for (int it = 0; blk < s.nblocks; ++it, blk += lg) {
             const BlockPos bp = block_pos(s, blk);
             issue_block(s, bp, R[0], smem, &mbar[0]);
             if (!finish_block(s, R[0], smem, &mbar[0], (uint32_t)(it & 1))) return;
@@ -296,9 +296,9 @@ __device__ void for_each_block(const DevSim& s, float4* smem, int buf_stride, Re
     }
     float4* buf[2] = {smem, smem + buf_stride};
     if (blk < s.nblocks) issue_block(s, block_pos(s, blk), R[0], buf[0], &mbar[0]);
-    for (int it = 0; blk < s.nblocks; ++it, blk += gridDim.x) {
+    for (int it = 0; blk < s.nblocks; ++it, blk += lg) {
         const int cur = it & 1;
-        const int64_t nb = blk + gridDim.x;
+        const int64_t nb = blk + lg;
         if (nb < s.nblocks) issue_block(s, block_pos(s, nb), R[cur ^ 1], buf[cur ^ 1], &mbar[cur ^ 1]);
         if (!finish_block(s, R[cur], buf[cur], &mbar[cur], (uint32_t)((it >> 1) & 1))) {
             // let the copies already issued for the next block land before leaving
@@ -447,8 +447,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// Block reduction of per-warp doubles into partials[q * kMaxPartials + blockIdx.x].
-__device__ void block_partials(const DevSim& s, const double* wv, int nq) {
+// Block reduction of per-warp doubles into partials[q * kMaxPartials + lb].
+__device__ void block_partials(const DevSim& s, int lb, const double* wv, int nq) {
     __shared__ double red[kBW][4];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
@@ -457,7 +457,7 @@ __device__ void block_partials(const DevSim& s, const double* wv, int nq) {
     if (threadIdx.x < nq) {
         double t = 0.0;
         for (int k = 0; k < kBW; ++k) t += red[k][threadIdx.x];
-        s.partials[threadIdx.x * kMaxPartials + blockIdx.x] = t;
+        s.partials[threadIdx.x * kMaxPartials + lb] = t;
     }
 }
 
@@ -476,7 +476,7 @@ __device__ __forceinline__ void stencil_run(const Region& R, const WarpCell& wc,
 
 // MODE 0: Verlet list.  MODE 1: every particle of the 27-cell stencil (no stored list).
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
-__global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSim s) {
+__device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     extern __shared__ float4 smem[];
     __shared__ Region R[kStageBuffers];
     __shared__ __align__(8) uint64_t mbar[kStageBuffers];
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
     const float far = kFar;
     const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
     const uint4 sent = make_uint4(sv, sv, sv, sv);
-    for_each_block(s, smem, s.smax + 1, R, mbar, [&](const BlockPos& bp, const Region& Rc,
+    for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar, [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
         for (int cw = w; cw < kCells; cw += kBW) {
             const WarpCell wc = warp_cell(s, bp, cw);
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
     if (KE || ENERGY) {
         const double acc_ke = warp_sum_d((double)ke_sum - (double)ke_err);
         double wv[3] = {acc_ke, acc_u, acc_w};
-        block_partials(s, wv, 3);
+        block_partials(s, lb, wv, 3);
     }
 }
 
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSi
 // the store address advanced incrementally.
 constexpr int kRowWords = 4;  // 32-candidate words held per stencil row and pass
 
-__global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(DevSim s) {
+__device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
     extern __shared__ float4 smem[];
     __shared__ Region R[kStageBuffers];
@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(D
     uint32_t* list32 = reinterpret_cast<uint32_t*>(s.list);
     const int64_t rowstep = (int64_t)s.npad * 4;  // uint32 distance between kb rows
     // buffers are padded by 32 entries: word reads run past a row end
-    for_each_block(s, smem, s.smax + 1 + 32, R, mbar, [&](const BlockPos& bp, const Region& Rc,
+    for_each_block(s, lb, lg, smem, s.smax + 1 + 32, R, mbar, [&](const BlockPos& bp, const Region& Rc,
                                                            const float4* sm) {
         for (int cw = w; cw < kCells; cw += kBW) {
             const WarpCell wc = warp_cell(s, bp, cw);
@@ -883,13 +883,13 @@ __device__ __forceinline__ void pair_fp64(const DevSim& s, int si, const Pos64& 
 }
 
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
-__global__ void __launch_bounds__(kBW * 32) k_force64(DevSim s) {
+__device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
     extern __shared__ float4 smem[];
     __shared__ Region R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     Pos64* sm = reinterpret_cast<Pos64*>(smem);
     double acc_ke = 0.0, acc_u = 0.0, acc_w = 0.0;
-    for (int64_t blk = blockIdx.x; blk < s.nblocks; blk += gridDim.x) {
+    for (int64_t blk = lb; blk < s.nblocks; blk += lg) {
         const BlockPos bp = block_pos(s, blk);
         stage_block64(s, bp, R, sm);
         for (int cw = w; cw < kCells; cw += kBW) {
@@ -971,8 +971,49 @@ __global__ void __launch_bounds__(kBW * 32) k_force64(DevSim s) {
     }
     if (KE || ENERGY) {
         double wv3[3] = {acc_ke, acc_u, acc_w};
-        block_partials(s, wv3, 3);
+        block_partials(s, lb, wv3, 3);
     }
+}
+
+// ------------------------------------------------------------------ kernels ----
+// Each body runs for one system (DevSim by value) or, in the _many form, for the replica of
+// a batch that owns the CTA.
+
+template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+__global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSim s) {
+    force_body<MODE, ENERGY, KE, FSHIFT>(s, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+__global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force_many(ManySims m) {
+    __shared__ DevSim sh;
+    int lb, lg;
+    load_replica(m, sh, lb, lg);
+    force_body<MODE, ENERGY, KE, FSHIFT>(sh, lb, lg);
+}
+
+__global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(DevSim s) {
+    list_build_body(s, (int)blockIdx.x, (int)gridDim.x);
+}
+
+__global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build_many(ManySims m) {
+    __shared__ DevSim sh;
+    int lb, lg;
+    load_replica(m, sh, lb, lg);
+    list_build_body(sh, lb, lg);
+}
+
+template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+__global__ void __launch_bounds__(kBW * 32) k_force64(DevSim s) {
+    force64_body<MODE, ENERGY, KE, FSHIFT>(s, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+__global__ void __launch_bounds__(kBW * 32) k_force64_many(ManySims m) {
+    __shared__ DevSim sh;
+    int lb, lg;
+    load_replica(m, sh, lb, lg);
+    force64_body<MODE, ENERGY, KE, FSHIFT>(sh, lb, lg);
 }
 
 // Opt every kernel with dynamic shared memory into the largest size the device allows
@@ -1008,6 +1049,17 @@ void run_force(const DevSim& s, cudaStream_t st) {
     }
 }
 
+template <int MODE, bool KE, bool FS>
+void run_force_many(const ManySims& m, int total, bool fp64, int smax_max, cudaStream_t st) {
+    if (fp64) {
+        size_t bytes = (size_t)(smax_max + 1) * sizeof(Pos64);
+        k_force64_many<MODE, false, KE, FS><<<total, kBW * 32, bytes, st>>>(m);
+    } else {
+        size_t bytes = kStageBuffers * (size_t)(smax_max + 1 + (MODE == 1 ? 32 : 0)) * sizeof(float4);
+        k_force_many<MODE, false, KE, FS><<<total, kBW * 32, bytes, st>>>(m);
+    }
+}
+
 template <int MODE>
 void run_force_mode(const DevSim& s, cudaStream_t st, bool energy, bool ke, bool fs) {
     if (fs) {
@@ -1029,6 +1081,10 @@ template <int MODE, bool E, bool KE, bool FS>
 void prep_one() {
     set_smem(k_force<MODE, E, KE, FS>);
     set_smem(k_force64<MODE, E, KE, FS>);
+    if (!E) {
+        set_smem(k_force_many<MODE, E, KE, FS>);
+        set_smem(k_force64_many<MODE, E, KE, FS>);
+    }
 }
 
 template <int MODE>
@@ -1052,6 +1108,7 @@ bool prepare_force_kernels() {
     prep_mode<0>();
     prep_mode<1>();
     set_smem(k_list_build);
+    set_smem(k_list_build_many);
     return g_smem_ok;
 }
 
@@ -1079,6 +1136,32 @@ void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke) {
         run_force_mode<0>(s, st, energy, ke, fs);
     else
         run_force_mode<1>(s, st, energy, ke, fs);
+}
+
+void launch_force_many(const ManySims& m, int total, bool fp64, bool cell, bool ke, bool fshift,
+                       int smax_max, cudaStream_t st) {
+    if (cell) {
+        if (ke) {
+            if (fshift) run_force_many<1, true, true>(m, total, fp64, smax_max, st);
+            else run_force_many<1, true, false>(m, total, fp64, smax_max, st);
+        } else {
+            if (fshift) run_force_many<1, false, true>(m, total, fp64, smax_max, st);
+            else run_force_many<1, false, false>(m, total, fp64, smax_max, st);
+        }
+    } else {
+        if (ke) {
+            if (fshift) run_force_many<0, true, true>(m, total, fp64, smax_max, st);
+            else run_force_many<0, true, false>(m, total, fp64, smax_max, st);
+        } else {
+            if (fshift) run_force_many<0, false, true>(m, total, fp64, smax_max, st);
+            else run_force_many<0, false, false>(m, total, fp64, smax_max, st);
+        }
+    }
+}
+
+void launch_list_build_many(const ManySims& m, int total, int smax_max, cudaStream_t st) {
+    const size_t bytes = kStageBuffers * (size_t)(smax_max + 1 + 32) * sizeof(float4);
+    k_list_build_many<<<total, kBW * 32, bytes, st>>>(m);
 }
 
 void launch_list_build(const DevSim& s, cudaStream_t st) {

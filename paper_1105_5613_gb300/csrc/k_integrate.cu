@@ -67,7 +67,7 @@ __global__ void k_begin(DevSim s, int64_t nsteps, double dt, int kind, double T0
 }
 
 template <bool FP64>
-__global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
+__device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) {
     const DevScalars* sc = s.sc;
     const double dt = sc->dt;
     const double snext = sc->s_next;
@@ -80,8 +80,8 @@ __global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
     const float vtofix = pow2f(kVelExp);
     const float dtx = dtf * pow2f(s.kexp > 126 ? 126 : s.kexp);  // k <= 61 in practice
     bool need = false;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < s.n;
+         i += (int64_t)lg * blockDim.x) {
         float4 rb = s.relb[i];
         int wb = __float_as_int(rb.w);
         int spc = wb & 1;
@@ -151,6 +151,19 @@ __global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
     if (__any_sync(FULL, need) && (threadIdx.x & 31) == 0) s.sc->rebuild = 1;
 }
 
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
+    integrate_body<FP64>(s, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_integrate_many(ManySims m) {
+    __shared__ DevSim sh;
+    int lb, lg;
+    load_replica(m, sh, lb, lg);
+    integrate_body<FP64>(sh, lb, lg);
+}
+
 // Sum partials[q][0 .. nb) for q < nq in a fixed order (one block of 256 threads).
 __device__ void sum_partials(const DevSim& s, int nb, int nq, double* out) {
     __shared__ double red[8][256];
@@ -170,10 +183,11 @@ __device__ void sum_partials(const DevSim& s, int nb, int nq, double* out) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_finalize(DevSim s, int nb, int ke) {
+// The force kernel's grid_cell blocks wrote the kinetic-energy partials.
+__device__ __forceinline__ void finalize_body(const DevSim& s, int ke) {
     __shared__ double K[1];
     DevScalars* sc = s.sc;
-    if (ke) sum_partials(s, nb, 1, K);
+    if (ke) sum_partials(s, s.grid_cell, 1, K);
     if (threadIdx.x != 0) return;
     const int k = sc->step_in_call;
     const double dt = sc->dt;
@@ -202,6 +216,15 @@ __global__ void __launch_bounds__(256) k_finalize(DevSim s, int nb, int ke) {
         sc->n_rebuilds += 1;
         sc->rebuild = 0;
     }
+}
+
+__global__ void __launch_bounds__(256) k_finalize(DevSim s, int ke) { finalize_body(s, ke); }
+
+__global__ void __launch_bounds__(256) k_finalize_many(ManySims m, int ke) {
+    __shared__ DevSim sh;
+    int lb, lg;
+    load_replica(m, sh, lb, lg);
+    finalize_body(sh, ke);
 }
 
 template <bool FP64>
@@ -680,7 +703,18 @@ void launch_integrate(const DevSim& s, cudaStream_t st) {
 }
 
 void launch_finalize(const DevSim& s, cudaStream_t st, bool ke) {
-    k_finalize<<<1, 256, 0, st>>>(s, s.grid_cell, ke ? 1 : 0);
+    k_finalize<<<1, 256, 0, st>>>(s, ke ? 1 : 0);
+}
+
+void launch_integrate_many(const ManySims& part, int total, bool fp64, cudaStream_t st) {
+    if (fp64)
+        k_integrate_many<true><<<total, kThreads, 0, st>>>(part);
+    else
+        k_integrate_many<false><<<total, kThreads, 0, st>>>(part);
+}
+
+void launch_finalize_many(const ManySims& one, int nrep, bool ke, cudaStream_t st) {
+    k_finalize_many<<<nrep, 256, 0, st>>>(one, ke ? 1 : 0);
 }
 
 void launch_finish(const DevSim& s, cudaStream_t st) {

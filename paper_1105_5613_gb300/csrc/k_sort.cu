@@ -20,19 +20,23 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 
-__global__ void __launch_bounds__(kThreads) k_zero(DevSim s) {
+__host__ __device__ __forceinline__ int scan_chunks(const DevSim& s) {
+    return (int)((s.ncell + kScanChunk - 1) / kScanChunk);
+}
+
+__device__ __forceinline__ void zero_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= s.ncell;
-         c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c <= s.ncell;
+         c += (int64_t)lg * blockDim.x) {
         s.count[c] = 0;
         s.cursor[c] = 0;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_bin(DevSim s) {
+__device__ __forceinline__ void bin_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < s.n;
+         i += (int64_t)lg * blockDim.x) {
         int ax = cell_axis((long long)s.x[i], s.D[0], s.nc[0]);
         int ay = cell_axis((long long)s.x[s.npad + i], s.D[1], s.nc[1]);
         int az = cell_axis((long long)s.x[2 * s.npad + i], s.D[2], s.nc[2]);
@@ -72,10 +76,11 @@ __device__ int block_scan_excl(int v, int& total) {
 }
 
 // pass 1: per-chunk sums of count[0 .. ncell)
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(DevSim s, int nchunks) {
+__device__ __forceinline__ void scan_reduce_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
+    const int nchunks = scan_chunks(s);
     __shared__ int red[kScanThreads / 32];
-    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int ch = lb; ch < nchunks; ch += lg) {
         int64_t base = (int64_t)ch * kScanChunk + (int64_t)threadIdx.x * kScanItems;
         int acc = 0;
 #pragma unroll
@@ -98,8 +103,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(DevSim s, int nchu
 }
 
 // pass 2: exclusive scan of the chunk sums (one block)
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(DevSim s, int nchunks) {
+__device__ __forceinline__ void scan_top_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
+    const int nchunks = scan_chunks(s);
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -118,9 +124,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(DevSim s, int nchunks
 }
 
 // pass 3: per-chunk exclusive scan plus chunk offset -> cell_start
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(DevSim s, int nchunks) {
+__device__ __forceinline__ void scan_down_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
-    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int nchunks = scan_chunks(s);
+    for (int ch = lb; ch < nchunks; ch += lg) {
         int64_t base = (int64_t)ch * kScanChunk + (int64_t)threadIdx.x * kScanItems;
         int vals[kScanItems];
         int acc = 0;
@@ -139,13 +146,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(DevSim s, int nchunk
             ex += vals[k];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) s.cell_start[s.ncell] = (int32_t)s.n;
+    if (lb == 0 && threadIdx.x == 0) s.cell_start[s.ncell] = (int32_t)s.n;
 }
 
-__global__ void __launch_bounds__(kThreads) k_scatter(DevSim s) {
+__device__ __forceinline__ void scatter_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < s.n;
+         i += (int64_t)lg * blockDim.x) {
         int c = s.key[i];
         int slot = s.cell_start[c] + atomicAdd(&s.cursor[c], 1);
         s.perm_tmp[slot] = (int32_t)i;
@@ -153,11 +160,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter(DevSim s) {
 }
 
 // Order each cell's particles by id: rank = number of smaller ids in the cell.
-__global__ void __launch_bounds__(kThreads) k_cellsort(DevSim s) {
+__device__ __forceinline__ void cellsort_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < s.ncell;
+    const int64_t nwarps = (int64_t)lg * (blockDim.x >> 5);
+    for (int64_t c = (lb * (int64_t)blockDim.x + threadIdx.x) >> 5; c < s.ncell;
          c += nwarps) {
         int start = s.cell_start[c];
         int cnt = s.cell_start[c + 1] - start;
@@ -182,10 +189,10 @@ __global__ void __launch_bounds__(kThreads) k_cellsort(DevSim s) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_gather(DevSim s) {
+__device__ __forceinline__ void gather_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
-         k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t k = lb * (int64_t)blockDim.x + threadIdx.x; k < s.n;
+         k += (int64_t)lg * blockDim.x) {
         int64_t o = s.perm[k];
         int c = s.key[o];
         int ax, ay, az;
@@ -209,10 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_gather(DevSim s) {
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_copyback(DevSim s) {
+__device__ __forceinline__ void copyback_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
-         k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t k = lb * (int64_t)blockDim.x + threadIdx.x; k < s.n;
+         k += (int64_t)lg * blockDim.x) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             s.x[d * s.npad + k] = s.x2[d * s.npad + k];
@@ -224,21 +231,47 @@ __global__ void __launch_bounds__(kThreads) k_copyback(DevSim s) {
     }
 }
 
+BBMD_ONE_AND_MANY(kThreads, k_zero, zero_body)
+BBMD_ONE_AND_MANY(kThreads, k_bin, bin_body)
+BBMD_ONE_AND_MANY(kScanThreads, k_scan_reduce, scan_reduce_body)
+BBMD_ONE_AND_MANY(kScanThreads, k_scan_top, scan_top_body)
+BBMD_ONE_AND_MANY(kScanThreads, k_scan_down, scan_down_body)
+BBMD_ONE_AND_MANY(kThreads, k_scatter, scatter_body)
+BBMD_ONE_AND_MANY(kThreads, k_cellsort, cellsort_body)
+BBMD_ONE_AND_MANY(kThreads, k_gather, gather_body)
+BBMD_ONE_AND_MANY(kThreads, k_copyback, copyback_body)
+
 }  // namespace
 
+int scan_grid(const DevSim& s) {
+    const int nchunks = scan_chunks(s);
+    return nchunks < 1 ? 1 : (nchunks < 1024 ? nchunks : 1024);
+}
+
 void launch_rebuild_chain(const DevSim& s, cudaStream_t st) {
-    int nchunks = (int)((s.ncell + kScanChunk - 1) / kScanChunk);
-    int gscan = nchunks < 1024 ? nchunks : 1024;
-    if (gscan < 1) gscan = 1;
+    const int gscan = scan_grid(s);
     k_zero<<<s.grid_part, kThreads, 0, st>>>(s);
     k_bin<<<s.grid_part, kThreads, 0, st>>>(s);
-    k_scan_reduce<<<gscan, kScanThreads, 0, st>>>(s, nchunks);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(s, nchunks);
-    k_scan_down<<<gscan, kScanThreads, 0, st>>>(s, nchunks);
+    k_scan_reduce<<<gscan, kScanThreads, 0, st>>>(s);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(s);
+    k_scan_down<<<gscan, kScanThreads, 0, st>>>(s);
     k_scatter<<<s.grid_part, kThreads, 0, st>>>(s);
     k_cellsort<<<s.grid_part, kThreads, 0, st>>>(s);
     k_gather<<<s.grid_part, kThreads, 0, st>>>(s);
     k_copyback<<<s.grid_part, kThreads, 0, st>>>(s);
+}
+
+void launch_rebuild_chain_many(const ManySims& part, const ManySims& scan, const ManySims& one,
+                               int total_part, int total_scan, int nrep, cudaStream_t st) {
+    k_zero_many<<<total_part, kThreads, 0, st>>>(part);
+    k_bin_many<<<total_part, kThreads, 0, st>>>(part);
+    k_scan_reduce_many<<<total_scan, kScanThreads, 0, st>>>(scan);
+    k_scan_top_many<<<nrep, kScanThreads, 0, st>>>(one);
+    k_scan_down_many<<<total_scan, kScanThreads, 0, st>>>(scan);
+    k_scatter_many<<<total_part, kThreads, 0, st>>>(part);
+    k_cellsort_many<<<total_part, kThreads, 0, st>>>(part);
+    k_gather_many<<<total_part, kThreads, 0, st>>>(part);
+    k_copyback_many<<<total_part, kThreads, 0, st>>>(part);
 }
 
 }  // namespace bbmd

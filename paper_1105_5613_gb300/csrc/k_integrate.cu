@@ -15,6 +15,8 @@
 // Mixed precision keeps positions and velocities in 64-bit fixed point and forms every
 // increment in FP32; no FP64 arithmetic runs per particle per step (GB300 issues FP64 at
 // a small fraction of the FP32 rate).
+#include <algorithm>
+
 #include "bbmd_internal.cuh"
 
 namespace bbmd {
@@ -79,9 +81,15 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
     const float vscale = pow2f(-kVelExp);
     const float vtofix = pow2f(kVelExp);
     const float dtx = dtf * pow2f(s.kexp > 126 ? 126 : s.kexp);  // k <= 61 in practice
-    bool need = false;
-    for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < s.n;
-         i += (int64_t)lg * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const float half_thr = 0.5f * s.disp_thr;
+    bool near = false;
+    for (int64_t base = lb * (int64_t)blockDim.x + (threadIdx.x & ~31); base < s.n;
+         base += (int64_t)lg * blockDim.x) {
+        const int64_t i = base + lane;
+        int c = -1;  // build cell (-1: no particle)
+        float disp = 0.f;
+        if (i < s.n) {
         // every input of the particle is loaded before the first store (the stores could
         // alias the later loads as far as the compiler knows)
         const float4 rb = s.relb[i];
@@ -100,7 +108,7 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
         }
         int wb = __float_as_int(rb.w);
         int spc = wb & 1;
-        int c = wb >> 1;
+        c = wb >> 1;
         int a3[3];
         a3[0] = c % s.nc[0];
         a3[1] = (c / s.nc[0]) % s.nc[1];
@@ -158,16 +166,91 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
         }
         if (!(vmax < 1000.f)) set_status(s, ST_VEL_RANGE);
         s.rel[i] = make_float4(r[0], r[1], r[2], (float)spc);
-        float ex = r[0] - rb.x, ey = r[1] - rb.y, ez = r[2] - rb.z;
-        if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > s.disp2) need = true;
+        // displacement since the last build (read by the rebuild trigger)
+        const float ex = r[0] - rb.x, ey = r[1] - rb.y, ez = r[2] - rb.z;
+        disp = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+        }
+        if (c >= 0) s.disp[i] = disp;
+        near = near || disp > half_thr;
     }
-    if (__any_sync(FULL, need) && (threadIdx.x & 31) == 0) s.sc->rebuild = 1;
+    // the trigger's passes run only in steps where some particle got near the threshold
+    if (__any_sync(FULL, near) && lane == 0) s.sc->near = 1;
 }
 
 template <bool FP64>
 __global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
     integrate_body<FP64>(s, (int)blockIdx.x, (int)gridDim.x);
 }
+
+// Rebuild trigger.  A pair missing from the lists (or a neighbour outside the cell stencil,
+// in cell mode) can interact only if its two particles moved, since the build, by more
+// than the skin together, and both lie in the same or neighbouring build cells.  So the
+// lists stay valid while, for every build cell c, the sum of its two largest displacements
+// and the sum of its largest with the largest of each of its 26 neighbours stay within
+// the skin.  Pass 1 finds the two largest displacements of every cell (a warp per cell,
+// the particles of a cell being contiguous); pass 2 checks the sums, starting only from
+// cells whose largest displacement exceeds half the threshold.
+__device__ __forceinline__ void top2_insert(float v, float& a, float& b) {
+    if (v > a) {
+        b = a;
+        a = v;
+    } else if (v > b) {
+        b = v;
+    }
+}
+
+__device__ __forceinline__ void celltop_body(const DevSim& s, int lb, int lg) {
+    if (!s.sc->near) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)lg * (blockDim.x >> 5);
+    for (int64_t c = (lb * (int64_t)blockDim.x + threadIdx.x) >> 5; c < s.ncell; c += nwarps) {
+        const int st = s.cell_start[c], en = s.cell_start[c + 1];
+        float a = 0.f, b = 0.f;
+        for (int k = st + lane; k < en; k += 32) top2_insert(s.disp[k], a, b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oa = __shfl_xor_sync(FULL, a, o);
+            const float ob = __shfl_xor_sync(FULL, b, o);
+            top2_insert(oa, a, b);
+            top2_insert(ob, a, b);
+        }
+        if (lane == 0) s.mtop[c] = make_float2(a, b);
+    }
+}
+
+__device__ __forceinline__ void check_body(const DevSim& s, int lb, int lg) {
+    DevScalars* sc = s.sc;
+    if (!sc->near) return;
+    const float thr = s.disp_thr;
+    bool need = false;
+    for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < s.ncell;
+         c += (int64_t)lg * blockDim.x) {
+        const float2 m = s.mtop[c];
+        if (m.x <= 0.5f * thr) continue;
+        float mx = m.y;  // the cell's own second largest
+        int a[3];
+        cell_coords((int)c, s.nc, a[0], a[1], a[2]);
+        for (int dz = -1; dz <= 1; ++dz) {
+            int z = a[2] + dz;
+            z = z < 0 ? z + s.nc[2] : (z >= s.nc[2] ? z - s.nc[2] : z);
+            for (int dy = -1; dy <= 1; ++dy) {
+                int y = a[1] + dy;
+                y = y < 0 ? y + s.nc[1] : (y >= s.nc[1] ? y - s.nc[1] : y);
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if ((dx | dy | dz) == 0) continue;
+                    int x = a[0] + dx;
+                    x = x < 0 ? x + s.nc[0] : (x >= s.nc[0] ? x - s.nc[0] : x);
+                    mx = fmaxf(mx, s.mtop[(z * s.nc[1] + y) * s.nc[0] + x].x);
+                }
+            }
+        }
+        if (m.x + mx > thr) need = true;
+    }
+    if (need) sc->rebuild = 1;
+}
+
+BBMD_ONE_AND_MANY(kThreads, k_celltop, celltop_body)
+BBMD_ONE_AND_MANY(kThreads, k_check, check_body)
 
 template <bool FP64>
 __global__ void __launch_bounds__(kThreads) k_integrate_many(ManySims m) {
@@ -225,6 +308,7 @@ __device__ __forceinline__ void finalize_body(const DevSim& s, int ke) {
     sc->pending = 1;
     sc->step_in_call = k + 1;
     sc->step += 1;
+    sc->near = 0;
     if (sc->rebuild) {
         sc->n_rebuilds += 1;
         sc->rebuild = 0;
@@ -713,6 +797,17 @@ void launch_integrate(const DevSim& s, cudaStream_t st) {
         k_integrate<true><<<s.grid_part, kThreads, 0, st>>>(s);
     else
         k_integrate<false><<<s.grid_part, kThreads, 0, st>>>(s);
+}
+
+void launch_check(const DevSim& s, cudaStream_t st) {
+    const int g = (int)std::min<int64_t>(s.grid_part, (s.ncell + kThreads - 1) / kThreads);
+    k_celltop<<<s.grid_part, kThreads, 0, st>>>(s);
+    k_check<<<g > 0 ? g : 1, kThreads, 0, st>>>(s);
+}
+
+void launch_check_many(const ManySims& part, int total, cudaStream_t st) {
+    k_celltop_many<<<total, kThreads, 0, st>>>(part);
+    k_check_many<<<total, kThreads, 0, st>>>(part);
 }
 
 void launch_finalize(const DevSim& s, cudaStream_t st, bool ke) {

@@ -194,22 +194,32 @@ __device__ __forceinline__ void gather_body(const DevSim& s, int lb, int lg) {
     for (int64_t k = lb * (int64_t)blockDim.x + threadIdx.x; k < s.n;
          k += (int64_t)lg * blockDim.x) {
         int64_t o = s.perm[k];
-        int c = s.key[o];
+        // all loads of the particle first (the stores could alias them for the compiler)
+        const int c = s.key[o];
+        uint64_t xv[3];
+        int64_t vv[3];
+        int32_t iv[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xv[d] = s.x[d * s.npad + o];
+            vv[d] = s.v[d * s.npad + o];
+            iv[d] = s.img[d * s.npad + o];
+        }
+        const int32_t idv = s.id[o];
+        const uint8_t spc = s.sp[o];
         int ax, ay, az;
         cell_coords(c, s.nc, ax, ay, az);
         int a3[3] = {ax, ay, az};
         float r[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            uint64_t xv = s.x[d * s.npad + o];
-            s.x2[d * s.npad + k] = xv;
-            s.v2[d * s.npad + k] = s.v[d * s.npad + o];
-            s.img2[d * s.npad + k] = s.img[d * s.npad + o];
-            long long rel = (long long)xv - frame_axis(a3[d], s.D[d]);
+            s.x2[d * s.npad + k] = xv[d];
+            s.v2[d * s.npad + k] = vv[d];
+            s.img2[d * s.npad + k] = iv[d];
+            long long rel = (long long)xv[d] - frame_axis(a3[d], s.D[d]);
             r[d] = i64_to_f32(rel) * s.sx;
         }
-        s.id2[k] = s.id[o];
-        uint8_t spc = s.sp[o];
+        s.id2[k] = idv;
         s.sp2[k] = spc;
         s.relb[k] = make_float4(r[0], r[1], r[2], __int_as_float((c << 1) | spc));
         s.rel[k] = make_float4(r[0], r[1], r[2], (float)spc);
@@ -220,14 +230,25 @@ __device__ __forceinline__ void copyback_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
     for (int64_t k = lb * (int64_t)blockDim.x + threadIdx.x; k < s.n;
          k += (int64_t)lg * blockDim.x) {
+        uint64_t xv[3];
+        int64_t vv[3];
+        int32_t iv[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            s.x[d * s.npad + k] = s.x2[d * s.npad + k];
-            s.v[d * s.npad + k] = s.v2[d * s.npad + k];
-            s.img[d * s.npad + k] = s.img2[d * s.npad + k];
+            xv[d] = s.x2[d * s.npad + k];
+            vv[d] = s.v2[d * s.npad + k];
+            iv[d] = s.img2[d * s.npad + k];
         }
-        s.id[k] = s.id2[k];
-        s.sp[k] = s.sp2[k];
+        const int32_t idv = s.id2[k];
+        const uint8_t spc = s.sp2[k];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            s.x[d * s.npad + k] = xv[d];
+            s.v[d * s.npad + k] = vv[d];
+            s.img[d * s.npad + k] = iv[d];
+        }
+        s.id[k] = idv;
+        s.sp[k] = spc;
     }
 }
 

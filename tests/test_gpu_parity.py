@@ -438,3 +438,25 @@ def test_full_size_sampled(ncell):
     offo, nbro = oracle.neighbors_subset(xfix, sp, L, k, R2, idx, 2.8)
     assert np.array_equal(off, offo) and np.array_equal(nbr, nbro)
     sim.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_lists_stay_valid_until_the_rebuild_trigger(mode):
+    """The rebuild trigger (two neighbouring cells' largest displacements summing beyond the
+    skin) keeps every interacting pair in the aged lists / cell stencils: at many points of
+    a hot NVE run the forces from the aged structures equal those of a fresh handle built at
+    the same positions (only the FP32 summation order differs)."""
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.05, T=3.0, nbr_mode=mode)
+    p.block_z = sim.info()["block_z"]
+    worst = 0.0
+    for k in range(40):
+        sim.step(3, 0.005)
+        gp, gv, _ = sim.get_state()
+        twin = bbmd.Sim(p, n, L, sp, gp, gv)
+        e = force_errors(sim.get_forces(), twin.get_forces())
+        twin.close()
+        worst = max(worst, float(e.max()))
+    rebuilds = sim.observe(0)["n_rebuilds"]
+    sim.close()
+    assert worst <= 1e-4, worst
+    assert rebuilds >= 5  # the run did cross several rebuilds

@@ -353,7 +353,9 @@ def run_ours(args):
         "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
         "block_z": block_z,
         "rebuilds_per_step": nreb / nprof,
-        "gpu_launches": args.steps * 13 + 2,
+        # per step: integrate, 2 trigger kernels, 9 gated sort kernels, gated list build,
+        # force, finalize (one graph); plus begin and finish of the call
+        "gpu_launches": args.steps * 15 + 2,
         "clocks": clocks,
         "fp64": fp64,
         "large": large,

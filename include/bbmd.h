@@ -234,6 +234,12 @@ bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
  * potential energy (half of each pair energy).  Recomputes on the device; synchronising. */
 bbmd_status bbmd_get_forces(bbmd_sim* sim, double* F, double* u);
 
+/* Forces (m x 3) and, when u is non-NULL, per-particle energies (m) of the particles ids[0..m)
+ * at the current positions (recomputed on the device as in bbmd_get_forces); copies only
+ * the m results to the host, for sampling large systems.  Synchronising. */
+bbmd_status bbmd_get_forces_ids(bbmd_sim* sim, const int64_t* ids, int64_t m, double* F,
+                                double* u);
+
 /* Cell of each particle at the last rebuild (n entries, id order):
  * (az * ncy + ay) * ncx + ax.  Synchronising. */
 bbmd_status bbmd_get_cells(bbmd_sim* sim, int64_t* cell);

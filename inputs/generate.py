@@ -93,6 +93,18 @@ def fcc_lattice(ncell: int, L: float) -> np.ndarray:
     return pos.reshape(-1, 3)
 
 
+def fcc_sites(ncell: int, L: float, idx: np.ndarray) -> np.ndarray:
+    """Positions of the FCC sites ``idx`` (same numbering and values as
+    :func:`fcc_lattice`), without building the whole lattice."""
+    n = int(ncell)
+    a = L / n
+    idx = np.asarray(idx, dtype=np.int64)
+    b = idx % 4
+    c = idx // 4
+    cells = np.stack([c % n, (c // n) % n, c // (n * n)], axis=1).astype(np.float64)
+    return (cells + _FCC_BASIS[b] + 0.25) * a
+
+
 def assign_species(n: int, n_b: int, seed: int) -> np.ndarray:
     """Seeded random choice of which ``n_b`` of ``n`` particles are species B (label 1).
 

@@ -85,7 +85,7 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_minimize",
            "bbmd_get_state", "bbmd_set_state", "bbmd_get_forces", "bbmd_get_cells",
            "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error",
-           "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_create_batch", "bbmd_step_batch",
+           "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_get_forces_ids", "bbmd_create_batch", "bbmd_step_batch",
            "bbmd_batch_replica", "bbmd_batch_size", "bbmd_batch_set_branches",
            "bbmd_destroy_batch",
            "bbmd_batch_last_error"]
@@ -125,6 +125,8 @@ def load(path: str | None = None):
     L.bbmd_set_state.restype = C.c_int
     L.bbmd_get_forces.argtypes = [vp, P(d), P(d)]
     L.bbmd_get_forces.restype = C.c_int
+    L.bbmd_get_forces_ids.argtypes = [vp, P(i64), i64, P(d), P(d)]
+    L.bbmd_get_forces_ids.restype = C.c_int
     L.bbmd_get_cells.argtypes = [vp, P(i64)]
     L.bbmd_get_cells.restype = C.c_int
     L.bbmd_get_neighbors.argtypes = [vp, P(i64), i64, P(i64), P(i64), i64]
@@ -327,6 +329,15 @@ class Sim:
         F = np.zeros((self.n, 3))
         u = np.zeros(self.n) if energies else None
         _check(self.h, load().bbmd_get_forces(self.h, _dp(F), _dp(u)))
+        return (F, u) if energies else F
+
+    def get_forces_ids(self, ids, energies=False):
+        """Forces (m, 3) (and energies (m,)) of the particles ids only."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        F = np.zeros((ids.size, 3))
+        u = np.zeros(ids.size) if energies else None
+        _check(self.h, load().bbmd_get_forces_ids(self.h, ids.ctypes.data_as(C.POINTER(C.c_int64)),
+                                                  int(ids.size), _dp(F), _dp(u)))
         return (F, u) if energies else F
 
     def get_cells(self):

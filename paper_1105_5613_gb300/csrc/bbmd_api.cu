@@ -862,6 +862,40 @@ bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
     return read_status(sim);
 }
 
+bbmd_status bbmd_get_forces_ids(bbmd_sim* sim, const int64_t* ids, int64_t m, double* F,
+                                double* u) {
+    if (!sim || !ids || !F || m < 0) return BBMD_ERR_ARG;
+    const int64_t n = sim->d.n;
+    for (int64_t t = 0; t < m; ++t)
+        if (ids[t] < 0 || ids[t] >= n) return fail(sim, BBMD_ERR_ARG, "ids must be in [0, n)");
+    if (m == 0) return BBMD_OK;
+    launch_force(sim->d, sim->st, u != nullptr, false);
+    int32_t* slot_of = (int32_t*)dev_alloc(sim, (size_t)n * 4);
+    int64_t* dids = (int64_t*)dev_alloc(sim, (size_t)m * 8);
+    double* tf = (double*)dev_alloc(sim, (size_t)m * 24);
+    double* tu = u ? (double*)dev_alloc(sim, (size_t)m * 8) : nullptr;
+    bbmd_status rc = BBMD_OK;
+    if (!slot_of || !dids || !tf || (u && !tu)) rc = fail(sim, BBMD_ERR_OOM, "get_forces_ids");
+    if (rc == BBMD_OK)
+        rc = cuda_check(sim, cudaMemcpyAsync(dids, ids, (size_t)m * 8, cudaMemcpyHostToDevice, sim->st), "H2D");
+    if (rc == BBMD_OK) {
+        launch_slot_of(sim->d, sim->st, slot_of);
+        launch_forces_of_ids(sim->d, sim->st, slot_of, dids, m, tf, tu);
+        rc = cuda_check(sim, cudaGetLastError(), "forces of ids");
+    }
+    if (rc == BBMD_OK)
+        rc = cuda_check(sim, cudaMemcpyAsync(F, tf, (size_t)m * 24, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK && u)
+        rc = cuda_check(sim, cudaMemcpyAsync(u, tu, (size_t)m * 8, cudaMemcpyDeviceToHost, sim->st), "D2H");
+    if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+    dev_free(sim, slot_of);
+    dev_free(sim, dids);
+    dev_free(sim, tf);
+    dev_free(sim, tu);
+    if (rc != BBMD_OK) return rc;
+    return read_status(sim);
+}
+
 bbmd_status bbmd_get_forces(bbmd_sim* sim, double* F, double* u) {
     if (!sim || !F) return BBMD_ERR_ARG;
     const int64_t n = sim->d.n;

@@ -320,6 +320,8 @@ void launch_pack_state(const DevSim& s, cudaStream_t st, const double* pos, cons
                        const int32_t* img, bool species_from_current);
 void launch_unpack_forces(const DevSim& s, cudaStream_t st, double* F, double* u);
 void launch_unpack_cells(const DevSim& s, cudaStream_t st, int64_t* cell);
+void launch_forces_of_ids(const DevSim& s, cudaStream_t st, const int32_t* slot_of,
+                          const int64_t* ids, int64_t m, double* F, double* u);
 // Neighbour lists by id.  sel: slots of the m requested particles (NULL = all, output
 // in id order).
 void launch_slot_of(const DevSim& s, cudaStream_t st, int32_t* slot_of);

@@ -636,6 +636,25 @@ __global__ void __launch_bounds__(kThreads) k_unpack_forces(DevSim s, double* F,
     }
 }
 
+// Forces of the particles ids[0..m) (slot_of: sorted position of each id).
+__global__ void __launch_bounds__(kThreads) k_forces_of_ids(DevSim s, const int32_t* slot_of,
+                                                           const int64_t* ids, int64_t m,
+                                                           double* F, double* u) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = slot_of[ids[t]];
+        if (s.precision == BBMD_PREC_FP64) {
+            for (int d = 0; d < 3; ++d) F[3 * t + d] = s.Fd[d * s.npad + k];
+        } else {
+            const float4 f = s.F[k];
+            F[3 * t] = f.x;
+            F[3 * t + 1] = f.y;
+            F[3 * t + 2] = f.z;
+        }
+        if (u) u[t] = s.ud[k];
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_unpack_cells(DevSim s, int64_t* cell) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
          k += (int64_t)gridDim.x * blockDim.x)
@@ -897,6 +916,12 @@ void launch_pack_state(const DevSim& s, cudaStream_t st, const double* pos, cons
 
 void launch_unpack_forces(const DevSim& s, cudaStream_t st, double* F, double* u) {
     k_unpack_forces<<<s.grid_part, kThreads, 0, st>>>(s, F, u);
+}
+
+void launch_forces_of_ids(const DevSim& s, cudaStream_t st, const int32_t* slot_of,
+                          const int64_t* ids, int64_t m, double* F, double* u) {
+    const int g = (int)std::min<int64_t>(s.grid_part, (m + kThreads - 1) / kThreads);
+    k_forces_of_ids<<<g > 0 ? g : 1, kThreads, 0, st>>>(s, slot_of, ids, m, F, u);
 }
 
 void launch_unpack_cells(const DevSim& s, cudaStream_t st, int64_t* cell) {

@@ -56,3 +56,10 @@ def test_replica_sizes_range_and_rounding():
     assert len(ns) == 64 and all(2048 <= n <= 32768 and n % 5 == 0 for n in ns)
     assert len(set(ns)) > 50  # uneven sizes
     assert ns == gen.replica_sizes(64, 2048, 32768, 0)
+
+
+def test_fcc_sites_equal_the_lattice():
+    L = gen.box_for(4 * 9 ** 3, 1.2)
+    full = gen.fcc_lattice(9, L)
+    idx = np.random.default_rng(0).permutation(full.shape[0])[:500]
+    assert np.array_equal(gen.fcc_sites(9, L, idx), full[idx])

@@ -255,18 +255,27 @@ def run_ours(args):
     for t, a in zip(pin, (pos, vel, img)):
         t.numpy()[...] = a
     hp, hv, hi = (t.numpy() for t in pin)
+    outp = [torch.empty(a.shape, dtype=torch.float64 if a.dtype == np.float64 else torch.int32,
+                        pin_memory=True) for a in (pos, vel, img)]
+    gp, gv, gi = (t.numpy() for t in outp)
     ke2 = max(1, args.e2e_steps)
+    obs_bytes = ctypes_sizeof_obs(bbmd)
     barrier()
     t0 = time.perf_counter()
+    # upload of the state from pinned host memory, then every step: one step and the read
+    # back of its result (kinetic energy, temperature, momentum, step count), then the
+    # download of the final state into pinned host memory
     sim.set_state(hp, hv, hi)
-    sim.step(ke2, DT, therm(ke2))
-    o2 = sim.observe(bbmd.OBS_ENERGY)
-    gp, gv, gi = sim.get_state()
+    for k in range(ke2):
+        sim.step(1, DT, (bbmd.THERMO_NH, ramp_T(step + k), ramp_T(step + k + 1), TAU))
+        sim.observe(0)
+    sim.get_state(out=(gp, gv, gi))
     t1 = time.perf_counter()
     barrier()
+    step += ke2
     e2e_s = t1 - t0
     h2d = hp.nbytes + hv.nbytes + hi.nbytes
-    d2h = gp.nbytes + gv.nbytes + gi.nbytes + 8 * 16
+    d2h = gp.nbytes + gv.nbytes + gi.nbytes + ke2 * obs_bytes
     sim.close()
 
     # ---- FP64 form on the same workload (a few steps) ----
@@ -458,6 +467,12 @@ def run_replicas(args, stream):
             "T_first_last": Ts}
 
 
+def ctypes_sizeof_obs(bbmd):
+    import ctypes
+
+    return ctypes.sizeof(bbmd.bbmd_obs)
+
+
 def force_traffic(n):
     """DRAM bytes (read + write) per k_force launch from the committed ncu summary, scaled to
     n particles; None when the kernel source changed since those counters were taken."""
@@ -539,7 +554,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--equil", type=int, default=400,
                     help="untimed equilibration steps at T=2.0 before the ramp")
     ap.add_argument("--fp64-steps", type=int, default=3)

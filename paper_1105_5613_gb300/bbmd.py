@@ -308,10 +308,17 @@ class Sim:
     def minimize(self, nsteps, hmax=1e-3, dmax=0.05):
         _check(self.h, load().bbmd_minimize(self.h, int(nsteps), float(hmax), float(dmax)))
 
-    def get_state(self):
-        pos = np.zeros((self.n, 3))
-        vel = np.zeros((self.n, 3))
-        img = np.zeros((self.n, 3), dtype=np.int32)
+    def get_state(self, out=None):
+        """(pos, vel, image) in id order; out: three arrays to fill instead (e.g. pinned)."""
+        if out is not None:
+            pos, vel, img = out
+            assert pos.shape == (self.n, 3) and pos.dtype == np.float64 and pos.flags.c_contiguous
+            assert vel.shape == (self.n, 3) and vel.dtype == np.float64 and vel.flags.c_contiguous
+            assert img.shape == (self.n, 3) and img.dtype == np.int32 and img.flags.c_contiguous
+        else:
+            pos = np.zeros((self.n, 3))
+            vel = np.zeros((self.n, 3))
+            img = np.zeros((self.n, 3), dtype=np.int32)
         _check(self.h, load().bbmd_get_state(self.h, _dp(pos), _dp(vel),
                                              img.ctypes.data_as(C.POINTER(C.c_int32))))
         return pos, vel, img

@@ -87,6 +87,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 struct Region {
     int off[kRegion + 1];      // prefix of staged counts (clamped to smax); off[kRegion] = total
     int start[kRegion];        // first particle of each region cell
+    int cnt[kRegion];          // particles of each region cell
     float hi[kRegion][3];      // frame offset of each cell (FP32 rounding of the exact value)
     float lo[kRegion][3];      // exact residual of that rounding (non-zero across the seam)
     long long fr[kRegion][3];  // FP64 form: frame point + seam image of each cell
@@ -94,6 +95,10 @@ struct Region {
 };
 
 // ------------------------------------------------ TMA bulk copies and mbarriers ----
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -203,6 +208,7 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
         const int st = s.cell_start[nb];
         cnt = s.cell_start[nb + 1] - st;
         R.start[tid] = st;
+        R.cnt[tid] = cnt;
     }
     // every lane of the warps that cover the region takes part in the scan (lanes past the
     // region carry a count of zero)
@@ -501,9 +507,28 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                                                       const float4* sm) {
         for (int cw = w; cw < kCells; cw += kBW) {
             const WarpCell wc = warp_cell(s, bp, cw);
-            const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
-            const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+            const int i0 = wc.valid ? Rc.start[wc.rq] : 0;
+            const int cnt = wc.valid ? Rc.cnt[wc.rq] : 0;
             const int self0 = Rc.off[wc.rq];
+            // the warp's next cell: its first list rows, velocities and row count go to L2
+            // now, so that its prologue does not wait on DRAM
+            if (MODE == 0 && cw + kBW < kCells) {
+                const WarpCell wn = warp_cell(s, bp, cw + kBW);
+                if (wn.valid) {
+                    const int j0 = Rc.start[wn.rq];
+                    if (lane < Rc.cnt[wn.rq]) {
+                        const uint4* lq = reinterpret_cast<const uint4*>(s.list) + j0 + lane;
+                        prefetch_l2(lq);
+                        prefetch_l2(lq + s.npad);
+                        if (KE) {
+                            prefetch_l2(s.v + j0 + lane);
+                            prefetch_l2(s.v + s.npad + j0 + lane);
+                            prefetch_l2(s.v + 2 * s.npad + j0 + lane);
+                        }
+                    }
+                    if (lane == 0) prefetch_l2(s.cellmax + j0);
+                }
+            }
             for (int ch = 0; ch * 32 < cnt; ++ch) {
                 const int li = ch * 32 + lane;
                 const bool act = li < cnt;
@@ -681,8 +706,8 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                                                            const float4* sm) {
         for (int cw = w; cw < kCells; cw += kBW) {
             const WarpCell wc = warp_cell(s, bp, cw);
-            const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
-            const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+            const int i0 = wc.valid ? Rc.start[wc.rq] : 0;
+            const int cnt = wc.valid ? Rc.cnt[wc.rq] : 0;
             const int self0 = Rc.off[wc.rq];
             for (int ch = 0; ch * 32 < cnt; ++ch) {
                 const int li = ch * 32 + lane;

@@ -254,8 +254,9 @@ bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int
 
 /* Re-run the block-shape autotuner of bbmd_create on the current state (creation times the
  * shapes on the initial state, e.g. a lattice; a liquid can favour another shape), rebuild
- * the lists for the shape chosen and recompute the forces.  Nothing changes when
- * params.block_z fixed the shape.  Synchronising. */
+ * the lists for the shape chosen and recompute the forces.  The list build is weighted by
+ * the rebuilds per step observed since the previous tuning (creation weighs it 1/4).
+ * Nothing changes when params.block_z fixed the shape.  Synchronising. */
 bbmd_status bbmd_tune(bbmd_sim* sim);
 
 /* Force a rebuild (binning, reorder and list) at the current positions. */

@@ -33,6 +33,7 @@ struct bbmd_sim {
     int sticky = 0;
     int nsm = 1;
     int graph_gen = 0;               // bumped whenever captured launch arguments go stale
+    long long tune_step = 0, tune_rebuilds = 0;  // counters at the last shape tuning
     double mean_cell = 0.0;          // mean particles per cell
     std::vector<int> shapes;         // block shapes that fit (candidates of the autotuner)
     float shape_ms[4][2] = {};       // autotuner: per kShapes entry, force and list-build ms
@@ -286,7 +287,7 @@ bbmd_status rebuild_now(bbmd_sim* sim) {
 // whole box); keep the shape of least force + list / 4 (a rebuild about every four steps).
 // A shape whose staged region or lists overflow is dropped.  The lists of the chosen shape
 // are rebuilt at the end, over the whole box.
-bbmd_status autotune_shape(bbmd_sim* sim) {
+bbmd_status autotune_shape(bbmd_sim* sim, float rebuild_rate = 0.25f) {
     DevSim& D = sim->d;
     const bool verlet = D.nbr_mode == BBMD_NBR_VERLET;
     cudaEvent_t ev[4];
@@ -335,7 +336,7 @@ bbmd_status autotune_shape(bbmd_sim* sim) {
             CK(cudaMemcpyAsync(&D.sc->status, &status0, sizeof(int), cudaMemcpyHostToDevice, sim->st));
             continue;
         }
-        const float cost = tf + (verlet ? 0.25f * tl : 0.f);
+        const float cost = tf + (verlet ? rebuild_rate * tl : 0.f);
         if (best < 0 || cost < best_cost) {
             best = bz;
             best_cost = cost;
@@ -1003,8 +1004,18 @@ bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int
 bbmd_status bbmd_tune(bbmd_sim* sim) {
     if (!sim) return BBMD_ERR_ARG;
     if (sim->shapes.size() < 2) return BBMD_OK;
+    // weight of the list build: the rebuilds per step seen since the last tuning (a rebuild
+    // about every four steps when fewer than 20 steps were taken)
+    DevScalars scl;
+    CK(cudaMemcpyAsync(&scl, sim->d.sc, sizeof(scl), cudaMemcpyDeviceToHost, sim->st));
+    CK(cudaStreamSynchronize(sim->st));
+    float rate = 0.25f;
+    const long long dsteps = scl.step - sim->tune_step, dreb = scl.n_rebuilds - sim->tune_rebuilds;
+    if (dsteps >= 20) rate = std::min(1.0f, std::max(0.02f, (float)dreb / (float)dsteps));
+    sim->tune_step = scl.step;
+    sim->tune_rebuilds = scl.n_rebuilds;
     bbmd_status rc = rebuild_now(sim);
-    if (rc == BBMD_OK) rc = autotune_shape(sim);
+    if (rc == BBMD_OK) rc = autotune_shape(sim, rate);
     free_graphs(sim);  // the captured launches carry the previous shape
     if (rc == BBMD_OK) rc = refresh_forces_and_K(sim);
     if (rc != BBMD_OK) return rc;

@@ -782,17 +782,35 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                         for (int q = 0; q < kRowWords; ++q) {
                             unsigned bits = m[q];
                             const unsigned base = (unsigned)(r0 + 32 * q);
-                            while (bits) {
+                            // entries go out in pairs (one 32-bit store each; entries beyond
+                            // the capacity are counted, not stored): a pending odd entry is
+                            // completed by the word's first bit, then two bits per iteration;
+                            // an odd last bit stays pending
+                            if ((len & 1) && bits) {
                                 const int u = __clz(bits);
                                 bits &= 0x7fffffffu >> u;
-                                const unsigned t = base + (unsigned)u;
-                                // an odd entry completes a pair: one 32-bit store (entries
-                                // beyond the capacity are counted, not stored)
                                 const int wi = len >> 1;
-                                if ((len & 1) && wi < lcap2)
-                                    row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] = pend | (t << 16);
-                                pend = t;
+                                if (wi < lcap2)
+                                    row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
+                                        pend | ((base + (unsigned)u) << 16);
                                 ++len;
+                            }
+                            while (bits) {
+                                const int u1 = __clz(bits);
+                                bits &= 0x7fffffffu >> u1;
+                                const unsigned t1 = base + (unsigned)u1;
+                                if (!bits) {
+                                    pend = t1;
+                                    ++len;
+                                    break;
+                                }
+                                const int u2 = __clz(bits);
+                                bits &= 0x7fffffffu >> u2;
+                                const int wi = len >> 1;
+                                if (wi < lcap2)
+                                    row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
+                                        t1 | ((base + (unsigned)u2) << 16);
+                                len += 2;
                             }
                         }
                     }

@@ -173,7 +173,12 @@ def run_ours(args):
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    b.build()
+    if rank == 0:
+        b.build()  # one rank compiles (a no-op when the library is up to date)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
     bbmd.load()
     n = 4 * args.ncell ** 3
     L = gen.box_for(n, 1.2)

@@ -108,15 +108,17 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, path):
+    def __init__(self, path, gpu=None):
         self.path = path
+        self.gpu = gpu  # nvidia-smi index of this rank's GPU (None: every GPU)
         self.proc = None
 
     def __enter__(self):
         try:
             self.f = open(self.path, "w")
+            sel = [] if self.gpu is None else ["-i", str(self.gpu)]
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                ["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -226,8 +228,10 @@ def run_ours(args):
 
     # ---- device-timed region ----
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    local_gpu = torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else None
     clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else os.devnull)
+                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else os.devnull,
+                       gpu=local_gpu)
     barrier()
     torch.cuda.synchronize()
     with clk:

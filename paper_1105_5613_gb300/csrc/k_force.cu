@@ -503,7 +503,8 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     const float far = kFar;
     const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
     const uint4 sent = make_uint4(sv, sv, sv, sv);
-    for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar, [&](const BlockPos& bp, const Region& Rc,
+    for_each_block(s, lb, lg, smem, s.smax + 1 + (MODE == 1 ? 32 : 0), R, mbar,
+                   [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
         for (int cw = w; cw < kCells; cw += kBW) {
             const WarpCell wc = warp_cell(s, bp, cw);

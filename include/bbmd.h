@@ -178,7 +178,8 @@ typedef struct {
  * alloc: NULL = cudaMalloc.
  * On success *out receives the handle, the first list is built and the forces of the
  * initial positions are computed. */
-/* Non-finite input positions or velocities are rejected with BBMD_ERR_ARG. */
+/* Non-finite input positions or velocities and species labels other than 0 and 1 are
+ * rejected with BBMD_ERR_ARG, before any device work. */
 bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3],
                         const uint8_t* species, const double* pos, const double* vel,
                         double T0, uint64_t seed, void* stream, const bbmd_alloc* alloc,

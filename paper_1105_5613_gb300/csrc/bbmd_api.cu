@@ -403,6 +403,11 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
         return vs;
     }
     if (!species) return BBMD_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (species[i] > 1) {
+            std::fprintf(stderr, "bbmd_create: species labels must be 0 or 1\n");
+            return BBMD_ERR_ARG;
+        }
     if (!(T0 >= 0.0)) return BBMD_ERR_ARG;
     if (!all_finite(pos, 3 * n) || !all_finite(vel, 3 * n)) {
         std::fprintf(stderr, "bbmd_create: non-finite positions or velocities\n");

@@ -225,12 +225,11 @@ int shape_smax(const bbmd_sim* sim, int bz) {
     return (smax + 31) / 32 * 32;
 }
 
-// The staged region must fit in shared memory (list build: + 32 records of slack; FP64
-// form: 32-byte records) and its offsets in uint16 (the sentinel is smax itself).
+// The staged region and its sentinel record must fit in shared memory (FP64 form: 32-byte
+// records) and its offsets in uint16 (the sentinel is smax itself).
 bool shape_fits(const bbmd_sim* sim, int bz) {
     const int smax = shape_smax(sim, bz);
-    const size_t bytes = sim->P.precision == BBMD_PREC_FP64 ? (size_t)(smax + 1) * 32
-                                                            : (size_t)(smax + 33) * 16;
+    const size_t bytes = (size_t)(smax + 1) * (sim->P.precision == BBMD_PREC_FP64 ? 32 : 16);
     return smax <= 65000 && bytes <= 200 * 1024;
 }
 

@@ -317,6 +317,13 @@ __device__ void for_each_block(const DevSim& s, int lb, int lg, float4* smem, in
     }
 }
 
+// Particles of region cell q that were staged: all of them unless the region overflowed
+// the staged capacity (flagged, the results are then discarded), so a lane never reads
+// past the staged records.
+__device__ __forceinline__ int staged_count(const Region& R, int q) {
+    return min(R.cnt[q], R.off[q + 1] - R.off[q]);
+}
+
 // Global index of staged entry t (rare path): binary search of the region prefix.
 __device__ __forceinline__ int64_t staged_global(const Region& R, int t) {
     int lo = 0, hi = kRegion - 1;
@@ -480,6 +487,92 @@ __device__ __forceinline__ void stencil_run(const Region& R, const WarpCell& wc,
     re = R.off[q0 + 3];
 }
 
+// ------------------------------------------------------- stencil compaction ----
+// A stencil candidate farther than the reach from the bounding box of the warp's particles
+// pairs with none of them.  Such candidates are dropped, 32 at a time, before the per-lane
+// tests. The survivors keep their stencil order in a per-warp ring of staged indices. The
+// lists and force sums therefore come out exactly as when every candidate is tested.
+// The reach carries a relative margin of 2^-9. Against it, FP32 rounding of the staged
+// coordinates and of the box distance (about 1e-6 relative) is negligible. A dropped
+// candidate lies beyond the upper edge of the exact-test band for every lane.
+constexpr int kRing = 256;      // ring entries per warp (a power of two)
+constexpr int kRingWords = 4;   // 32-candidate words tested per pass
+
+struct WarpBox {
+    float lo[3], hi[3];
+};
+
+// Bounding box of the active lanes' positions.
+__device__ __forceinline__ WarpBox warp_box(float4 me, bool act) {
+    WarpBox b;
+    b.lo[0] = act ? me.x : kFar;
+    b.lo[1] = act ? me.y : kFar;
+    b.lo[2] = act ? me.z : kFar;
+    b.hi[0] = act ? me.x : -kFar;
+    b.hi[1] = act ? me.y : -kFar;
+    b.hi[2] = act ? me.z : -kFar;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            b.lo[d] = fminf(b.lo[d], __shfl_xor_sync(FULL, b.lo[d], o));
+            b.hi[d] = fmaxf(b.hi[d], __shfl_xor_sync(FULL, b.hi[d], o));
+        }
+    }
+    return b;
+}
+
+// Position in the warp's 27-cell stencil: row (dy, dz) and the next group start g0 in the
+// row's staged range [., re).
+struct StencilScan {
+    int row, g0, re;
+};
+
+// Advance to the next non-empty row if the current one is exhausted; false at the end.
+__device__ __forceinline__ bool scan_next(const Region& R, const WarpCell& wc, StencilScan& sc) {
+    while (sc.g0 >= sc.re) {
+        if (++sc.row == 9) return false;
+        stencil_run(R, wc, sc.row, sc.g0, sc.re);
+    }
+    return true;
+}
+
+// Candidates g0 + lane (below re) go through the box test; survivors are appended to the
+// ring at stream positions fill, fill + 1, ... in candidate order.  cself receives the
+// stream position of the lane's own particle when its group passes.
+__device__ __forceinline__ void compact_group(const float4* sm, int g0, int re, const WarpBox& bx,
+                                              float keepA, float keepB, uint32_t* ring, int& fill,
+                                              int self, int& cself, int lane) {
+    const int t = g0 + lane;
+    bool keep = false;
+    if (t < re) {
+        const float4 p = sm[t];
+        const float ex = fmaxf(fmaxf(bx.lo[0] - p.x, p.x - bx.hi[0]), 0.f);
+        const float ey = fmaxf(fmaxf(bx.lo[1] - p.y, p.y - bx.hi[1]), 0.f);
+        const float ez = fmaxf(fmaxf(bx.lo[2] - p.z, p.z - bx.hi[2]), 0.f);
+        keep = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < (p.w != 0.f ? keepB : keepA);
+    }
+    const unsigned bal = __ballot_sync(FULL, keep);
+    const int pos = fill + __popc(bal & ((1u << lane) - 1u));
+    if (keep) ring[pos & (kRing - 1)] = (uint32_t)t;
+    const int src = self - g0;
+    const int sp = __shfl_sync(FULL, pos, src & 31);
+    if (src >= 0 && src < 32) cself = sp;
+    fill += __popc(bal);
+}
+
+// After the last group: the rest of the last word points at the far sentinel record.
+__device__ __forceinline__ void ring_pad(uint32_t* ring, int fill, int lane, uint32_t sentinel) {
+    const int pe = (fill + 31) & ~31;
+    if (fill + lane < pe) ring[(fill + lane) & (kRing - 1)] = sentinel;
+}
+
+// Squared reach from the box for a candidate of species 0 / 1: the largest upper band edge
+// over the lane species, widened by 2^-9.
+__device__ __forceinline__ float keep_reach(const float* hi4, int sj) {
+    return fmaxf(hi4[sj], hi4[2 + sj]) * (1.0f + 0x1p-9f);
+}
+
 // MODE 0: Verlet list.  MODE 1: every particle of the 27-cell stencil (no stored list).
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
 __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
@@ -503,13 +596,15 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     const float far = kFar;
     const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
     const uint4 sent = make_uint4(sv, sv, sv, sv);
-    for_each_block(s, lb, lg, smem, s.smax + 1 + (MODE == 1 ? 32 : 0), R, mbar,
+    __shared__ __align__(16) uint32_t ring_all[MODE == 1 ? kBW : 1][MODE == 1 ? kRing : 4];
+    uint32_t* const ring = ring_all[MODE == 1 ? w : 0];
+    for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar,
                    [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
         for (int cw = w; cw < kCells; cw += kBW) {
             const WarpCell wc = warp_cell(s, bp, cw);
             const int i0 = wc.valid ? Rc.start[wc.rq] : 0;
-            const int cnt = wc.valid ? Rc.cnt[wc.rq] : 0;
+            const int cnt = wc.valid ? staged_count(Rc, wc.rq) : 0;
             const int self0 = Rc.off[wc.rq];
             // the warp's next cell: its first list rows, velocities and row count go to L2
             // now, so that its prologue does not wait on DRAM
@@ -543,8 +638,10 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                     e1 = __ldcs(lp + s.npad);
                     if (kListAhead > 2) e2 = __ldcs(lp + 2 * s.npad);
                 }
+                // (the stencil loop of MODE 1 needs every register: its velocities are read
+                // after it)
                 long long v0 = 0, v1 = 0, v2 = 0;
-                if (KE && act) {
+                if (KE && act && MODE == 0) {
                     v0 = s.v[gi];
                     v1 = s.v[s.npad + gi];
                     v2 = s.v[2 * s.npad + gi];
@@ -583,30 +680,49 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                         }
                     }
                 } else {
-                    // the stencil on the fly: 32 candidates at a time are filtered against
-                    // the cutoff into a bitmask (as the list build does against rc + skin),
-                    // band candidates decided by the exact rule, then the forces of the set
-                    // bits are added
+                    // the stencil on the fly: the candidates within reach of the warp's box,
+                    // 32 at a time, are filtered against the cutoff into a bitmask (as the
+                    // list build does against rc + skin), band candidates decided by the
+                    // exact rule, then the forces of the set bits are added
                     const float rcA = T.rlo0, drc = T.rlo1 - T.rlo0;
                     const float bandc = fmaxf(T.rhi0 - T.rlo0, T.rhi1 - T.rlo1);
-                    for (int row = 0; row < 9; ++row) {
-                        int rs, re;
-                        stencil_run(Rc, wc, row, rs, re);
-                        for (int t0 = rs; t0 < re; t0 += 32) {
+                    const WarpBox bx = warp_box(me, act);
+                    const float keepA = keep_reach(s.pt.rc2hi, 0), keepB = keep_reach(s.pt.rc2hi, 1);
+                    int fill = 0, done = 0, cself = -1;
+                    StencilScan sc = {-1, 0, 0};
+                    bool more = scan_next(Rc, wc, sc);
+                    while (more || done < fill) {
+                        while (more && fill - done < 32 * kRingWords) {
+                            compact_group(sm, sc.g0, sc.re, bx, keepA, keepB, ring, fill, self, cself,
+                                          lane);
+                            sc.g0 += 32;
+                            more = scan_next(Rc, wc, sc);
+                            if (!more) ring_pad(ring, fill, lane, (uint32_t)s.smax);
+                        }
+                        __syncwarp();
+                        const int nw = min(kRingWords, (fill - done + 31) >> 5);
+                        for (int q = 0; q < nw; ++q) {
+                            const int cq = done + 32 * q;
+                            const uint4* ip = reinterpret_cast<const uint4*>(ring + (cq & (kRing - 1)));
                             unsigned inw = 0u;
                             float near = far;
 #pragma unroll
-                            for (int u = 0; u < 32; ++u) {
-                                const float4 p = sm[t0 + u];
-                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                const float dlo =
-                                    fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, drc, rcA))));
-                                inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
-                                near = fminf(near, fabsf(dlo));
+                            for (int v = 0; v < 8; ++v) {
+                                const uint4 iv = ip[v];
+                                const uint32_t ix[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+                                for (int h = 0; h < 4; ++h) {
+                                    const float4 p = sm[ix[h]];
+                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                    const float dlo =
+                                        fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, drc, rcA))));
+                                    inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
+                                    near = fminf(near, fabsf(dlo));
+                                }
                             }
-                            const int nv = re - t0;
+                            const int nv = fill - cq;
                             unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
-                            if (self >= t0 && self < t0 + 32) valid &= ~(0x80000000u >> (self - t0));
+                            if (cself >= cq && cself < cq + 32) valid &= ~(0x80000000u >> (cself - cq));
                             if (!act) valid = 0u;
                             inw &= valid;
                             const bool chk = near < bandc && valid != 0u;
@@ -615,7 +731,8 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                                 while (bw) {
                                     const int u = __clz(bw);
                                     bw &= 0x7fffffffu >> u;
-                                    const float4 p = sm[t0 + u];
+                                    const int t = (int)ring[(cq + u) & (kRing - 1)];
+                                    const float4 p = sm[t];
                                     const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
                                     const float dlo =
                                         fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, drc, rcA))));
@@ -624,19 +741,21 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                                     inw &= ~bit;
                                     if (!min_image_copy(s, dx, dy, dz)) continue;
                                     const int tj = p.w != 0.f ? 1 : 0;
-                                    const int64_t gj = staged_global(Rc, t0 + u);
+                                    const int64_t gj = staged_global(Rc, t);
                                     if (r2_exact(s, gi, gj) < s.pt.rc2[si * 2 + tj]) inw |= bit;
                                 }
                             }
                             while (inw) {
                                 const int u = __clz(inw);
                                 inw &= 0x7fffffffu >> u;
-                                const float4 p = sm[t0 + u];
+                                const float4 p = sm[ring[(cq + u) & (kRing - 1)]];
                                 const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
                                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                                 pair_add<ENERGY, FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
                             }
                         }
+                        done += 32 * nw;
+                        __syncwarp();
                     }
                 }
                 float fx = -a.fx, fy = -a.fy, fz = -a.fz;
@@ -646,6 +765,11 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                     if (ENERGY) s.ud[gi] = 0.5 * a.u;
                 }
                 if (KE && act) {
+                    if (MODE == 1) {
+                        v0 = s.v[gi];
+                        v1 = s.v[s.npad + gi];
+                        v2 = s.v[2 * s.npad + gi];
+                    }
                     const float h = si ? hdt1 : hdt0;
                     const float m = si ? m1 : m0;
                     const float vx = fmaf(h, fx, i64_to_f32_fast(v0) * pow2f(-kVelExp));
@@ -695,6 +819,8 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lcap = s.lcap8 * 8;
     const int lcap2 = lcap >> 1;  // pair slots per particle
+    __shared__ __align__(16) uint32_t ring_all[kBW][kRing];
+    uint32_t* const ring = ring_all[w];
     if (threadIdx.x == 0)
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
     __syncthreads();
@@ -702,13 +828,12 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
     const unsigned sentpair = (unsigned)s.smax | ((unsigned)s.smax << 16);
     uint32_t* list32 = reinterpret_cast<uint32_t*>(s.list);
     const int64_t rowstep = (int64_t)s.npad * 4;  // uint32 distance between kb rows
-    // buffers are padded by 32 entries: word reads run past a row end
-    for_each_block(s, lb, lg, smem, s.smax + 1 + 32, R, mbar, [&](const BlockPos& bp, const Region& Rc,
+    for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar, [&](const BlockPos& bp, const Region& Rc,
                                                            const float4* sm) {
         for (int cw = w; cw < kCells; cw += kBW) {
             const WarpCell wc = warp_cell(s, bp, cw);
             const int i0 = wc.valid ? Rc.start[wc.rq] : 0;
-            const int cnt = wc.valid ? Rc.cnt[wc.rq] : 0;
+            const int cnt = wc.valid ? staged_count(Rc, wc.rq) : 0;
             const int self0 = Rc.off[wc.rq];
             for (int ch = 0; ch * 32 < cnt; ++ch) {
                 const int li = ch * 32 + lane;
@@ -728,20 +853,35 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                 // pair slot wi (entries 2 wi, 2 wi + 1) of this particle:
                 // row0[(wi >> 2) * rowstep + (wi & 3)]
                 uint32_t* const row0 = list32 + gi * 4;
-                for (int row = 0; row < 9; ++row) {
-                    int rs, re;
-                    stencil_run(Rc, wc, row, rs, re);
-                    for (int r0 = rs; r0 < re; r0 += 32 * kRowWords) {
-                        unsigned m[kRowWords];
+                const WarpBox bx = warp_box(me, act);
+                const float keepA = keep_reach(s.pt.R2hi, 0), keepB = keep_reach(s.pt.R2hi, 1);
+                int fill = 0, done = 0, cself = -1;
+                StencilScan sc = {-1, 0, 0};
+                bool more = scan_next(Rc, wc, sc);
+                while (more || done < fill) {
+                    while (more && fill - done < 32 * kRingWords) {
+                        compact_group(sm, sc.g0, sc.re, bx, keepA, keepB, ring, fill, self, cself, lane);
+                        sc.g0 += 32;
+                        more = scan_next(Rc, wc, sc);
+                        if (!more) ring_pad(ring, fill, lane, (uint32_t)s.smax);
+                    }
+                    __syncwarp();
+                    const int nw = min(kRingWords, (fill - done + 31) >> 5);
+                    unsigned m[kRingWords];
 #pragma unroll
-                        for (int q = 0; q < kRowWords; ++q) {
-                            const int t0 = r0 + 32 * q;
-                            unsigned inw = 0u;
-                            if (t0 < re) {  // warp-uniform
-                                float near = far;
+                    for (int q = 0; q < kRingWords; ++q) {
+                        unsigned inw = 0u;
+                        const int cq = done + 32 * q;
+                        if (q < nw) {  // warp-uniform
+                            const uint4* ip = reinterpret_cast<const uint4*>(ring + (cq & (kRing - 1)));
+                            float near = far;
 #pragma unroll
-                                for (int u = 0; u < 32; ++u) {
-                                    const float4 p = sm[t0 + u];
+                            for (int v = 0; v < 8; ++v) {
+                                const uint4 iv = ip[v];
+                                const uint32_t ix[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+                                for (int h = 0; h < 4; ++h) {
+                                    const float4 p = sm[ix[h]];
                                     const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
                                     // r^2 - R2lo(species of j), one FMA chain; sign = inside
                                     const float dlo = fmaf(dz, dz,
@@ -749,72 +889,75 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                                     inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
                                     near = fminf(near, fabsf(dlo));
                                 }
-                                const int nv = re - t0;
-                                unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
-                                if (self >= t0 && self < t0 + 32)
-                                    valid &= ~(0x80000000u >> (self - t0));
-                                if (!act) valid = 0u;
-                                inw &= valid;
-                                const bool chk = near < band && valid != 0u;
-                                if (__any_sync(FULL, chk) && chk) {
-                                    // the same FP32 value decides which candidates are in the
-                                    // band; those are decided by the exact rule
-                                    unsigned bw = valid;
-                                    while (bw) {
-                                        const int u = __clz(bw);
-                                        bw &= 0x7fffffffu >> u;
-                                        const float4 p = sm[t0 + u];
-                                        const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                        const float dlo = fmaf(dz, dz,
-                                                               fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
-                                        if (!(fabsf(dlo) < band)) continue;
-                                        const unsigned bit = 0x80000000u >> u;
-                                        inw &= ~bit;
-                                        if (!min_image_copy(s, dx, dy, dz)) continue;
-                                        const int tj = p.w != 0.f ? 1 : 0;
-                                        const int64_t gj = staged_global(Rc, t0 + u);
-                                        if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= bit;
-                                    }
+                            }
+                            const int nv = fill - cq;
+                            unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
+                            if (cself >= cq && cself < cq + 32) valid &= ~(0x80000000u >> (cself - cq));
+                            if (!act) valid = 0u;
+                            inw &= valid;
+                            const bool chk = near < band && valid != 0u;
+                            if (__any_sync(FULL, chk) && chk) {
+                                // the same FP32 value decides which candidates are in the
+                                // band; those are decided by the exact rule
+                                unsigned bw = valid;
+                                while (bw) {
+                                    const int u = __clz(bw);
+                                    bw &= 0x7fffffffu >> u;
+                                    const int t = (int)ring[(cq + u) & (kRing - 1)];
+                                    const float4 p = sm[t];
+                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                    const float dlo = fmaf(dz, dz,
+                                                           fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
+                                    if (!(fabsf(dlo) < band)) continue;
+                                    const unsigned bit = 0x80000000u >> u;
+                                    inw &= ~bit;
+                                    if (!min_image_copy(s, dx, dy, dz)) continue;
+                                    const int tj = p.w != 0.f ? 1 : 0;
+                                    const int64_t gj = staged_global(Rc, t);
+                                    if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= bit;
                                 }
                             }
-                            m[q] = inw;
                         }
+                        m[q] = inw;
+                    }
 #pragma unroll
-                        for (int q = 0; q < kRowWords; ++q) {
-                            unsigned bits = m[q];
-                            const unsigned base = (unsigned)(r0 + 32 * q);
-                            // entries go out in pairs (one 32-bit store each; entries beyond
-                            // the capacity are counted, not stored): a pending odd entry is
-                            // completed by the word's first bit, then two bits per iteration;
-                            // an odd last bit stays pending
-                            if ((len & 1) && bits) {
-                                const int u = __clz(bits);
-                                bits &= 0x7fffffffu >> u;
-                                const int wi = len >> 1;
-                                if (wi < lcap2)
-                                    row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
-                                        pend | ((base + (unsigned)u) << 16);
+                    for (int q = 0; q < kRingWords; ++q) {
+                        unsigned bits = m[q];
+                        const uint32_t* rq = ring;
+                        const int cq = done + 32 * q;
+                        // entries go out in pairs (one 32-bit store each; entries beyond the
+                        // capacity are counted, not stored): a pending odd entry is completed
+                        // by the word's first bit, then two bits per iteration; an odd last
+                        // bit stays pending
+                        if ((len & 1) && bits) {
+                            const int u = __clz(bits);
+                            bits &= 0x7fffffffu >> u;
+                            const int wi = len >> 1;
+                            if (wi < lcap2)
+                                row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
+                                    pend | (rq[(cq + u) & (kRing - 1)] << 16);
+                            ++len;
+                        }
+                        while (bits) {
+                            const int u1 = __clz(bits);
+                            bits &= 0x7fffffffu >> u1;
+                            const unsigned t1 = rq[(cq + u1) & (kRing - 1)];
+                            if (!bits) {
+                                pend = t1;
                                 ++len;
+                                break;
                             }
-                            while (bits) {
-                                const int u1 = __clz(bits);
-                                bits &= 0x7fffffffu >> u1;
-                                const unsigned t1 = base + (unsigned)u1;
-                                if (!bits) {
-                                    pend = t1;
-                                    ++len;
-                                    break;
-                                }
-                                const int u2 = __clz(bits);
-                                bits &= 0x7fffffffu >> u2;
-                                const int wi = len >> 1;
-                                if (wi < lcap2)
-                                    row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
-                                        t1 | ((base + (unsigned)u2) << 16);
-                                len += 2;
-                            }
+                            const int u2 = __clz(bits);
+                            bits &= 0x7fffffffu >> u2;
+                            const int wi = len >> 1;
+                            if (wi < lcap2)
+                                row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
+                                    t1 | (rq[(cq + u2) & (kRing - 1)] << 16);
+                            len += 2;
                         }
                     }
+                    done += 32 * nw;
+                    __syncwarp();
                 }
                 if (len > lcap) {
                     set_status(s, ST_LIST_OVERFLOW);
@@ -939,7 +1082,7 @@ __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
         for (int cw = w; cw < kCells; cw += kBW) {
         const WarpCell wc = warp_cell(s, bp, cw);
         const int i0 = wc.valid ? s.cell_start[wc.c] : 0;
-        const int cnt = wc.valid ? s.cell_start[wc.c + 1] - i0 : 0;
+        const int cnt = wc.valid ? staged_count(R, wc.rq) : 0;
         const int self0 = R.off[wc.rq];
         for (int ch = 0; ch * 32 < cnt; ++ch) {
             const int li = ch * 32 + lane;
@@ -1087,8 +1230,7 @@ void run_force(const DevSim& s, cudaStream_t st) {
         size_t bytes = (size_t)(s.smax + 1) * sizeof(Pos64);
         k_force64<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     } else {
-        // cell mode reads candidate words past a row end: 32 records of slack
-        size_t bytes = kStageBuffers * (size_t)(s.smax + 1 + (MODE == 1 ? 32 : 0)) * sizeof(float4);
+        size_t bytes = kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
         k_force<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
     }
 }
@@ -1099,7 +1241,7 @@ void run_force_many(const ManySims& m, int total, bool fp64, int smax_max, cudaS
         size_t bytes = (size_t)(smax_max + 1) * sizeof(Pos64);
         k_force64_many<MODE, false, KE, FS><<<total, kBW * 32, bytes, st>>>(m);
     } else {
-        size_t bytes = kStageBuffers * (size_t)(smax_max + 1 + (MODE == 1 ? 32 : 0)) * sizeof(float4);
+        size_t bytes = kStageBuffers * (size_t)(smax_max + 1) * sizeof(float4);
         k_force_many<MODE, false, KE, FS><<<total, kBW * 32, bytes, st>>>(m);
     }
 }
@@ -1169,7 +1311,7 @@ int force_blocks_per_sm(const DevSim& s) {
 
 int list_blocks_per_sm(const DevSim& s) {
     int nb = 0;
-    const size_t bytes = kStageBuffers * (size_t)(s.smax + 1 + 32) * sizeof(float4);
+    const size_t bytes = kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_list_build, kBW * 32, bytes);
     return nb > 0 ? nb : 1;
 }
@@ -1204,15 +1346,14 @@ void launch_force_many(const ManySims& m, int total, bool fp64, bool cell, bool 
 }
 
 void launch_list_build_many(const ManySims& m, int total, int smax_max, cudaStream_t st) {
-    const size_t bytes = kStageBuffers * (size_t)(smax_max + 1 + 32) * sizeof(float4);
+    const size_t bytes = kStageBuffers * (size_t)(smax_max + 1) * sizeof(float4);
     k_list_build_many<<<total, kBW * 32, bytes, st>>>(m);
 }
 
 void launch_list_build(const DevSim& s, cudaStream_t st) {
     if (s.nbr_mode != BBMD_NBR_VERLET) return;
-    // staging buffer(s), each: staged region + sentinel + 32 entries of slack for word reads
-    // past a row end
-    size_t bytes = kStageBuffers * (size_t)(s.smax + 1 + 32) * sizeof(float4);
+    // staging buffer(s), each: staged region + sentinel record
+    size_t bytes = kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
     k_list_build<<<s.grid_list, kBW * 32, bytes, st>>>(s);
 }
 

@@ -367,6 +367,7 @@ struct LaneTab {
     float e40, e41, vsh0, vsh1, fc0, fc1, rc0, rc1, sgl0, sgl1;
     float cpot;   // 0.5 for LJ force, 0 for soft sphere
     float cpe;    // 1 for LJ energy, 0 for soft sphere
+    float rm0, rm1, hw;  // list mode: middle of the band around rc^2, half-width (both j)
     int si;
 };
 
@@ -374,6 +375,9 @@ __device__ __forceinline__ void load_tab(const DevSim& s, int si, LaneTab& T) {
     const int k = si * 2;
     T.rlo0 = s.pt.rc2lo[k];      T.rlo1 = s.pt.rc2lo[k + 1];
     T.rhi0 = s.pt.rc2hi[k];      T.rhi1 = s.pt.rc2hi[k + 1];
+    T.rm0 = 0.5f * (T.rlo0 + T.rhi0);
+    T.rm1 = 0.5f * (T.rlo1 + T.rhi1);
+    T.hw = 0.5f * fmaxf(T.rhi0 - T.rlo0, T.rhi1 - T.rlo1);
     T.sig20 = s.pt.sig2[k];      T.sig21 = s.pt.sig2[k + 1];
     T.sgl0 = s.pt.sig2lo[k];     T.sgl1 = s.pt.sig2lo[k + 1];
     T.e480 = s.pt.eps48[k];      T.e481 = s.pt.eps48[k + 1];
@@ -419,17 +423,17 @@ __device__ __forceinline__ void pair_add(const LaneTab& T, bool b, float dx, flo
     }
 }
 
-// Fast path of one pair (i, staged t): interacting iff FP32 r^2 is below the lower edge
-// of the band around rc^2; a pair inside the band is only flagged for the exact fix-up.
+// Fast path of one list pair (i, staged t), classified by d = r^2 - (middle of the band
+// around rc^2 for the species of j): interacting iff d <= -hw; |d| < hw is the band,
+// left to the exact fix-up; the smallest |d| of a batch tells whether it has band pairs.
 template <bool ENERGY, bool FSHIFT>
-__device__ __forceinline__ void pair_fast(const LaneTab& T, float4 me, float4 p, bool valid, Acc& a,
-                                          bool& band) {
+__device__ __forceinline__ void pair_fast(const LaneTab& T, float4 me, float4 p, Acc& a, float& near) {
     float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const bool b = p.w != 0.f;
-    bool in = (r2 < (b ? T.rlo1 : T.rlo0)) && valid;
-    band = band || ((r2 < (b ? T.rhi1 : T.rhi0)) && !in && valid);
-    pair_add<ENERGY, FSHIFT>(T, b, dx, dy, dz, r2, in, a);
+    const float d = r2 - (b ? T.rm1 : T.rm0);
+    near = fminf(near, fabsf(d));
+    pair_add<ENERGY, FSHIFT>(T, b, dx, dy, dz, r2, d <= -T.hw, a);
 }
 
 // A staged copy is usable only in the minimum image (the 4x4x4 region holds a cell twice
@@ -447,7 +451,7 @@ __device__ __noinline__ void pair_band(const DevSim& s, const Region& R, const L
     float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const bool b = p.w != 0.f;
-    if (!valid || r2 < (b ? T.rlo1 : T.rlo0) || !(r2 < (b ? T.rhi1 : T.rhi0))) return;
+    if (!valid || !(fabsf(r2 - (b ? T.rm1 : T.rm0)) < T.hw)) return;
     if (!min_image_copy(s, dx, dy, dz)) return;
     int64_t gj = staged_global(R, t);
     if (r2_exact(s, gi, gj) < s.pt.rc2[T.si * 2 + (b ? 1 : 0)])
@@ -662,15 +666,16 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                         } else {
                             e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
                         }
-                        bool band = false;
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.x)], true, a, band);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.x)], true, a, band);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.y)], true, a, band);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.y)], true, a, band);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.z)], true, a, band);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.z)], true, a, band);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.w)], true, a, band);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.w)], true, a, band);
+                        float near = far;
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.x)], a, near);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.x)], a, near);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.y)], a, near);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.y)], a, near);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.z)], a, near);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.z)], a, near);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.w)], a, near);
+                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.w)], a, near);
+                        const bool band = near < T.hw;
                         if (__any_sync(FULL, band) && band) {
                             const unsigned ws[4] = {e.x, e.y, e.z, e.w};
                             for (int q = 0; q < 8; ++q) {
@@ -802,14 +807,13 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
 
 // ------------------------------------------------------------------ list build ----
 
-// Each lane tests every particle of its 27-cell stencil, 32 candidates at a time, with
+// Each lane tests the compacted candidates of its 27-cell stencil, 32 at a time, with
 // broadcast shared-memory reads: the sign of r^2 - R2lo(species of j) is shifted into a
 // 32-bit word (candidate u lands in bit 31 - u) and the smallest |r^2 - R2lo| of the word
 // is kept.  Only a word whose minimum falls inside the band goes through the exact rule,
-// candidate by candidate.  The set bits of one stencil row (up to kRowWords words) are
-// then written as list offsets, two entries per 32-bit store into [kb][npad][8] uint16,
-// the store address advanced incrementally.
-constexpr int kRowWords = 4;  // 32-candidate words held per stencil row and pass
+// candidate by candidate.  The set bits of up to kRingWords words are then written as
+// list offsets, two entries per 32-bit store into [kb][npad][8] uint16, at a row pointer
+// advanced once per four pairs.
 
 __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
@@ -853,6 +857,14 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                 // pair slot wi (entries 2 wi, 2 wi + 1) of this particle:
                 // row0[(wi >> 2) * rowstep + (wi & 3)]
                 uint32_t* const row0 = list32 + gi * 4;
+                // next pair slot wp and the start of its row
+                int wp = 0;
+                uint32_t* rowp = row0;
+                auto put_pair = [&](unsigned v) {
+                    if (wp < lcap2) rowp[wp & 3] = v;
+                    ++wp;
+                    if ((wp & 3) == 0) rowp += rowstep;
+                };
                 const WarpBox bx = warp_box(me, act);
                 const float keepA = keep_reach(s.pt.R2hi, 0), keepB = keep_reach(s.pt.R2hi, 1);
                 int fill = 0, done = 0, cself = -1;
@@ -923,25 +935,23 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
 #pragma unroll
                     for (int q = 0; q < kRingWords; ++q) {
                         unsigned bits = m[q];
-                        const uint32_t* rq = ring;
-                        const int cq = done + 32 * q;
-                        // entries go out in pairs (one 32-bit store each; entries beyond the
-                        // capacity are counted, not stored): a pending odd entry is completed
-                        // by the word's first bit, then two bits per iteration; an odd last
-                        // bit stays pending
+                        // the word's 32 ring entries are contiguous (word starts are
+                        // multiples of 32 in a ring of 256)
+                        const uint32_t* const rw = ring + ((done + 32 * q) & (kRing - 1));
+                        // entries go out in pairs (one 32-bit store each at the running row
+                        // pointer; entries beyond the capacity are counted, not stored): a
+                        // pending odd entry is completed by the word's first bit, then two
+                        // bits per iteration; an odd last bit stays pending
                         if ((len & 1) && bits) {
                             const int u = __clz(bits);
                             bits &= 0x7fffffffu >> u;
-                            const int wi = len >> 1;
-                            if (wi < lcap2)
-                                row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
-                                    pend | (rq[(cq + u) & (kRing - 1)] << 16);
+                            put_pair(pend | (rw[u] << 16));
                             ++len;
                         }
                         while (bits) {
                             const int u1 = __clz(bits);
                             bits &= 0x7fffffffu >> u1;
-                            const unsigned t1 = rq[(cq + u1) & (kRing - 1)];
+                            const unsigned t1 = rw[u1];
                             if (!bits) {
                                 pend = t1;
                                 ++len;
@@ -949,10 +959,7 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                             }
                             const int u2 = __clz(bits);
                             bits &= 0x7fffffffu >> u2;
-                            const int wi = len >> 1;
-                            if (wi < lcap2)
-                                row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] =
-                                    t1 | (rq[(cq + u2) & (kRing - 1)] << 16);
+                            put_pair(t1 | (rw[u2] << 16));
                             len += 2;
                         }
                     }

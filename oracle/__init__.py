@@ -34,7 +34,9 @@ def build(force: bool = False) -> str:
     ):
         cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", "-o", _LIB, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP serves only the all-core baseline form; without it that form runs serially
+        if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+            subprocess.run(cmd, check=True)
     return _LIB
 
 
@@ -92,6 +94,10 @@ def lib():
         L.orc_forces_brute.restype = None
         L.orc_forces_cells.argtypes = [i64, pd, pu8, pd, pP, pd, pd, pd, pd]
         L.orc_forces_cells.restype = i32
+        L.orc_forces_cells_full.argtypes = [i64, pd, pu8, pd, pP, pd, pd, pd]
+        L.orc_forces_cells_full.restype = i32
+        L.orc_threads.argtypes = []
+        L.orc_threads.restype = i32
         L.orc_fix_exponent.argtypes = [pd]
         L.orc_fix_exponent.restype = i32
         L.orc_quantize.argtypes = [i64, pd, i32, pd, pi64]
@@ -158,7 +164,9 @@ def pair(p: Params, a: int, b: int, r2: float):
 
 
 def forces(pos, species, L, p: Params, method: str = "brute"):
-    """Forces (n,3), per-particle energy u (n,), virial W, potential energy PE."""
+    """Forces (n,3), per-particle energy u (n,), virial W, potential energy PE.  method:
+    "brute" (O(N^2) definition), "cells" (linked cells, Newton's third law) or "cells_full"
+    (every particle sums its own stencil on every core; W is not computed)."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     sp = np.ascontiguousarray(species, dtype=np.uint8)
     n = pos.shape[0]
@@ -169,6 +177,12 @@ def forces(pos, species, L, p: Params, method: str = "brute"):
     if method == "brute":
         lib().orc_forces_brute(n, _dp(Lb), _u8p(sp), _dp(pos), C.byref(p), _dp(F), _dp(u),
                                C.byref(W), C.byref(PE))
+    elif method == "cells_full":  # all-core form: no virial
+        rc = lib().orc_forces_cells_full(n, _dp(Lb), _u8p(sp), _dp(pos), C.byref(p), _dp(F),
+                                         _dp(u), C.byref(PE))
+        if rc != 0:
+            raise ValueError("box too small for the cell search")
+        W.value = float("nan")
     else:
         rc = lib().orc_forces_cells(n, _dp(Lb), _u8p(sp), _dp(pos), C.byref(p), _dp(F),
                                     _dp(u), C.byref(W), C.byref(PE))
@@ -313,11 +327,18 @@ class MDState:
         return self.pos.shape[0]
 
 
-def md_run(st: MDState, nsteps: int, dt: float, thermo=None, use_cells: bool = False,
+def threads() -> int:
+    """Threads of the all-core force form (1 when built without OpenMP)."""
+    return int(lib().orc_threads())
+
+
+def md_run(st: MDState, nsteps: int, dt: float, thermo=None, use_cells=False,
            log: bool = False):
     """Advance ``st`` by ``nsteps`` velocity-Verlet steps (NVE, or Nose-Hoover when
-    ``thermo = (T_start, T_end, tau)``).  Returns the per-step log (nsteps, 5) of
-    {KE, PE, xi, eta, T_target} when ``log`` is set."""
+    ``thermo = (T_start, T_end, tau)``).  Forces by brute force, by linked cells
+    (``use_cells=True``) or by the all-core full-stencil form (``use_cells="all_cores"``).
+    Returns the per-step log (nsteps, 5) of {KE, PE, xi, eta, T_target} when ``log`` is
+    set."""
     th = None
     if thermo is not None:
         th = Thermo(1, float(thermo[0]), float(thermo[1]), float(thermo[2]))
@@ -325,7 +346,8 @@ def md_run(st: MDState, nsteps: int, dt: float, thermo=None, use_cells: bool = F
     rc = lib().orc_md_run(st.n, _dp(st.L), _u8p(st.species), C.byref(st.p), _dp(st.pos),
                           _dp(st.vel), _i32p(st.image), _dp(st.F), st.F_valid,
                           C.byref(st.nh), nsteps, dt, C.byref(th) if th else None,
-                          1 if use_cells else 0, _dp(lg) if log else None)
+                          2 if use_cells == "all_cores" else 1 if use_cells else 0,
+                          _dp(lg) if log else None)
     if rc != 0:
         raise ValueError("oracle md_run failed (box too small for cells?)")
     st.F_valid = 1

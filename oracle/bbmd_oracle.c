@@ -22,6 +22,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------------------------- */
 /* pair potential                                                                      */
@@ -173,6 +176,78 @@ int orc_forces_cells(int64_t n, const double L[3], const uint8_t* species, const
     free(next);
     free(cidx);
     return 0;
+}
+
+/* All-core form of the linked-cell forces, for the CPU baseline.  Every particle sums its
+ * own 27-cell stencil, so each pair is seen from both ends (a full neighbour set, as on the
+ * GPU).  Particles are then independent: the loop over them is shared out over every core
+ * (OpenMP), with one writer per force and per u_i.  PE is the serial sum of the u_i. */
+int orc_forces_cells_full(int64_t n, const double L[3], const uint8_t* species, const double* pos,
+                          const orc_params* p, double* F, double* u, double* PE) {
+    double rc = max_rcut(p);
+    int64_t nc[3];
+    for (int k = 0; k < 3; ++k) {
+        nc[k] = (int64_t)floor(L[k] / rc);
+        if (nc[k] < 3) return -1;
+    }
+    int64_t ncell = nc[0] * nc[1] * nc[2];
+    int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* cidx = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)(n > 0 ? n : 1));
+    double* ui = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) cidx[3 * i + k] = plain_cell(pos[3 * i + k], L[k], nc[k]);
+        int64_t c = (cidx[3 * i + 2] * nc[1] + cidx[3 * i + 1]) * nc[0] + cidx[3 * i];
+        next[i] = head[c];
+        head[c] = i;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double fi[3] = {0.0, 0.0, 0.0}, vi = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t ax = (cidx[3 * i] + dx + nc[0]) % nc[0];
+                    int64_t ay = (cidx[3 * i + 1] + dy + nc[1]) % nc[1];
+                    int64_t az = (cidx[3 * i + 2] + dz + nc[2]) % nc[2];
+                    int64_t c = (az * nc[1] + ay) * nc[0] + ax;
+                    for (int64_t j = head[c]; j >= 0; j = next[j]) {
+                        if (j == i) continue;
+                        double d[3];
+                        for (int k = 0; k < 3; ++k)
+                            d[k] = min_image(pos[3 * j + k] - pos[3 * i + k], L[k]);
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        double V, f;
+                        if (!orc_pair(p, species[i], species[j], r2, &V, &f)) continue;
+                        for (int k = 0; k < 3; ++k) fi[k] -= f * d[k];
+                        vi += 0.5 * V;
+                    }
+                }
+        if (F)
+            for (int k = 0; k < 3; ++k) F[3 * i + k] = fi[k];
+        ui[i] = vi;
+    }
+    double pe = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (u) u[i] = ui[i];
+        pe += ui[i];
+    }
+    if (PE) *PE = pe;
+    free(head);
+    free(next);
+    free(cidx);
+    free(ui);
+    return 0;
+}
+
+/* Threads the all-core form uses (1 when built without OpenMP). */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 int orc_forces_subset(int64_t n, const double L[3], const uint8_t* species, const double* pos,
@@ -456,6 +531,7 @@ double orc_kinetic(int64_t n, const uint8_t* species, const double* vel, const o
 static int compute_forces(int64_t n, const double L[3], const uint8_t* species,
                           const double* pos, const orc_params* p, double* F, double* PE,
                           int use_cells) {
+    if (use_cells == 2) return orc_forces_cells_full(n, L, species, pos, p, F, NULL, PE);
     if (use_cells) return orc_forces_cells(n, L, species, pos, p, F, NULL, NULL, PE);
     orc_forces_brute(n, L, species, pos, p, F, NULL, NULL, PE);
     return 0;

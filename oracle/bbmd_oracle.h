@@ -16,6 +16,7 @@
  *   orc_forces_brute    FCC lattice shell sum (coordination 12,6,24,12,24,...), zero
  *                       lattice forces, Newton's third law, translation invariance
  *   orc_forces_cells    equals orc_forces_brute (paper's search vs the O(N^2) definition)
+ *   orc_forces_cells_full  equals orc_forces_brute (all-core full-stencil form)
  *   orc_bin / orc_neighbors_*   brute-force set definition, symmetry, containment
  *   orc_md_run          time reversibility, dt^2 energy-error scaling, momentum,
  *                       Nose-Hoover free-gas ODE (scipy), extended-energy conservation
@@ -69,6 +70,15 @@ void orc_forces_brute(int64_t n, const double L[3], const uint8_t* species, cons
 int orc_forces_cells(int64_t n, const double L[3], const uint8_t* species, const double* pos,
                      const orc_params* p, double* F, double* u, double* W, double* PE);
 
+/* The same forces, per-particle energies and PE for the all-core CPU baseline: each
+ * particle sums its own 27-cell stencil (each pair seen from both ends), the particles
+ * shared out over every core.  -1 if the box holds fewer than 3 cells per axis. */
+int orc_forces_cells_full(int64_t n, const double L[3], const uint8_t* species, const double* pos,
+                          const orc_params* p, double* F, double* u, double* PE);
+
+/* Threads orc_forces_cells_full uses (1 when built without OpenMP). */
+int orc_threads(void);
+
 /* Forces, per-particle energy and virial share of the m particles idx[] only, by the
  * linked-cell search of Sec. 2.2 (both members of every pair visited, no Newton's third
  * law): F[3m], u[m] (may be NULL).  For spot checks of very large systems.  Returns -1
@@ -115,7 +125,8 @@ double orc_kinetic(int64_t n, const uint8_t* species, const double* vel, const o
  * splitting NH-half, kick, drift, force, kick, NH-half).  pos is wrapped into [0,L)
  * every step and image[3n] counts the box crossings.  F holds the forces of pos on
  * entry (computed if F_valid == 0) and on exit.  Forces by brute force when
- * use_cells == 0, else by orc_forces_cells.  If log is non-NULL it receives per step
+ * use_cells == 0, by orc_forces_cells when 1, by orc_forces_cells_full (every core) when
+ * 2.  If log is non-NULL it receives per step
  * {KE, PE, xi, eta, T_target} (5 doubles). */
 int orc_md_run(int64_t n, const double L[3], const uint8_t* species, const orc_params* p,
                double* pos, double* vel, int32_t* image, double* F, int F_valid,

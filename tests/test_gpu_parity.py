@@ -314,6 +314,14 @@ def test_errors_are_reported():
     with pytest.raises(bbmd.BBMDError) as ei:  # list capacity far too small
         bbmd.Sim(bbmd.ka_params(list_capacity=16), n, L, sp, pos, vel)
     assert ei.value.code == 5
+    # staged capacity far below one block region, in every shape, precision and mode: the
+    # kernels take only the staged particles and the overflow is reported
+    for prec in (bbmd.PREC_MIXED, bbmd.PREC_FP64):
+        for mode in (bbmd.NBR_VERLET, bbmd.NBR_CELL):
+            with pytest.raises(bbmd.BBMDError) as ei:
+                bbmd.Sim(bbmd.ka_params(precision=prec, nbr_mode=mode, stencil_capacity=64),
+                         n, L, sp, pos, vel)
+            assert ei.value.code == 5
     sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, pos, vel)
     with pytest.raises(bbmd.BBMDError):
         sim.step(10, -1.0)

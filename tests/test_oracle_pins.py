@@ -116,7 +116,7 @@ def test_fcc_shell_table_by_enumeration():
         assert int((norm == 2 * m).sum()) == c
 
 
-@pytest.mark.parametrize("method", ["brute", "cells"])
+@pytest.mark.parametrize("method", ["brute", "cells", "cells_full"])
 @pytest.mark.parametrize("shift", [0, 1, 2])
 def test_fcc_lattice_energy_and_zero_forces(method, shift):
     """Perfect all-A FCC crystal at rho=1.2: per-particle energy equals half the shell sum
@@ -185,6 +185,25 @@ def test_translation_invariance_and_cells_equal_brute():
     shifted = (pos + np.array([0.37, -1.21, 2.9])) % L
     Fs = oracle.forces(shifted, sp, L, p)[0]
     assert np.allclose(Fs, F, rtol=1e-9, atol=1e-9)
+
+
+def test_all_core_form_equals_brute_and_steps_like_cells():
+    """The all-core full-stencil form (the CPU baseline's second mode) gives the O(N^2)
+    definition's forces, energies and PE; a short Nose-Hoover run with it follows the
+    linked-cell run to rounding."""
+    pos, vel, sp, L = liquid(ncell=6, seed=7, shake=0.15)
+    p = oracle.ka_params()
+    F, u, W, PE = oracle.forces(pos, sp, L, p, "brute")
+    Ff, uf, Wf, PEf = oracle.forces(pos, sp, L, p, "cells_full")
+    assert np.allclose(Ff, F, rtol=1e-12, atol=1e-11)
+    assert np.allclose(uf, u, rtol=1e-12, atol=1e-12)
+    assert PEf == pytest.approx(PE, rel=1e-12)
+    assert oracle.threads() >= 1
+    a = oracle.MDState(pos, vel, sp, L, p)
+    b = oracle.MDState(pos, vel, sp, L, p)
+    oracle.md_run(a, 10, 0.005, thermo=(1.0, 1.0, 0.5), use_cells=True)
+    oracle.md_run(b, 10, 0.005, thermo=(1.0, 1.0, 0.5), use_cells="all_cores")
+    assert np.abs(a.pos - b.pos).max() < 1e-10 and np.abs(a.vel - b.vel).max() < 1e-9
 
 
 # ---------------------------------------------------------- cells and neighbour sets ----
@@ -407,7 +426,7 @@ def test_msd_fs_closed_forms():
     assert np.allclose(fs, np.cos(7.25 * dvec).mean(), rtol=1e-10)
 
 
-@pytest.mark.parametrize("method", ["brute", "cells"])
+@pytest.mark.parametrize("method", ["brute", "cells", "cells_full"])
 def test_two_body_systems_each_species_pair(method):
     """Many-body loop picks the right species pair: an isolated A-A, A-B or B-B dimer at
     r = 2^(1/6) sigma_ab has PE = -eps_ab - V_ab(rc) and zero force (energy shift)."""

@@ -227,7 +227,9 @@ bbmd_status bbmd_get_state(bbmd_sim* sim, double* pos, double* vel, int32_t* ima
 
 /* Replace positions (n x 3, quantised as in bbmd_create), velocities (n x 3) and image
  * counters (n x 3, NULL = zeros) from host arrays in id order.  Species are kept.  The
- * list is rebuilt and forces recomputed; the thermostat variables are kept. */
+ * list is rebuilt and forces recomputed; the thermostat variables are kept.  Non-finite
+ * positions or velocities (checked on the device after the upload, before anything of the
+ * state is replaced) return BBMD_ERR_ARG with the state unchanged.  Synchronising. */
 bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
                            const int32_t* image);
 

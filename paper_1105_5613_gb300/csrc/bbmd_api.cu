@@ -840,8 +840,6 @@ bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
                            const int32_t* image) {
     if (!sim || !pos || !vel) return BBMD_ERR_ARG;
     const int64_t n = sim->d.n;
-    if (!all_finite(pos, 3 * n) || !all_finite(vel, 3 * n))
-        return fail(sim, BBMD_ERR_ARG, "non-finite positions or velocities");
     double* tp = (double*)dev_alloc(sim, 3 * n * 8);
     double* tv = (double*)dev_alloc(sim, 3 * n * 8);
     int32_t* ti = image ? (int32_t*)dev_alloc(sim, 3 * n * 4) : nullptr;
@@ -853,6 +851,20 @@ bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
         rc = cuda_check(sim, cudaMemcpyAsync(tv, vel, 3 * n * 8, cudaMemcpyHostToDevice, sim->st), "H2D");
     if (rc == BBMD_OK && image)
         rc = cuda_check(sim, cudaMemcpyAsync(ti, image, 3 * n * 4, cudaMemcpyHostToDevice, sim->st), "H2D");
+    // the uploaded values are checked on the device (one pass over them at HBM speed, not
+    // a serial host scan) before anything of the state is replaced
+    if (rc == BBMD_OK) {
+        int bad = 0;
+        rc = cuda_check(sim, cudaMemsetAsync(&sim->d.sc->bad_input, 0, sizeof(int), sim->st), "memset");
+        if (rc == BBMD_OK) {
+            launch_check_finite(sim->d, sim->st, tp, 3 * n);
+            launch_check_finite(sim->d, sim->st, tv, 3 * n);
+            rc = cuda_check(sim, cudaMemcpyAsync(&bad, &sim->d.sc->bad_input, sizeof(int),
+                                                 cudaMemcpyDeviceToHost, sim->st), "D2H");
+        }
+        if (rc == BBMD_OK) rc = cuda_check(sim, cudaStreamSynchronize(sim->st), "sync");
+        if (rc == BBMD_OK && bad) rc = fail(sim, BBMD_ERR_ARG, "non-finite positions or velocities");
+    }
     if (rc == BBMD_OK) {
         launch_pack_state(sim->d, sim->st, tp, tv, ti, true);
         rc = cuda_check(sim, cudaGetLastError(), "pack");

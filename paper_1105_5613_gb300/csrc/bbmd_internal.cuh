@@ -53,6 +53,7 @@ struct DevScalars {
     int rebuild;             // 1: the gated rebuild kernels run in this step
     int near;                // 1: some displacement of this step exceeds half the threshold
     int status;              // ST_* bits
+    int bad_input;           // set_state: 1 if an uploaded value is not finite
 };
 
 struct PairTab {
@@ -319,6 +320,8 @@ void launch_unpack_state(const DevSim& s, cudaStream_t st, double* pos, double* 
 void launch_pack_state(const DevSim& s, cudaStream_t st, const double* pos, const double* vel,
                        const int32_t* img, bool species_from_current);
 void launch_unpack_forces(const DevSim& s, cudaStream_t st, double* F, double* u);
+// sc->bad_input = 1 if one of the m doubles at a (device) is not finite
+void launch_check_finite(const DevSim& s, cudaStream_t st, const double* a, int64_t m);
 void launch_unpack_cells(const DevSim& s, cudaStream_t st, int64_t* cell);
 void launch_forces_of_ids(const DevSim& s, cudaStream_t st, const int32_t* slot_of,
                           const int64_t* ids, int64_t m, double* F, double* u);

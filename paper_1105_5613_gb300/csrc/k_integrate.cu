@@ -605,6 +605,16 @@ __global__ void __launch_bounds__(kThreads) k_species_by_id(DevSim s) {
         s.sp2[s.id[k]] = s.sp[k];
 }
 
+// Uploaded state check: one CTA-wide vote per CTA, a flag written only when some value is
+// not finite.
+__global__ void __launch_bounds__(kThreads) k_check_finite(DevSim s, const double* a, int64_t m) {
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) s.sc->bad_input = 1;
+}
+
 __global__ void __launch_bounds__(kThreads) k_pack_state(DevSim s, const double* pos,
                                                         const double* vel, const int32_t* img) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
@@ -912,6 +922,10 @@ void launch_pack_state(const DevSim& s, cudaStream_t st, const double* pos, cons
                        const int32_t* img, bool species_from_current) {
     if (species_from_current) k_species_by_id<<<s.grid_part, kThreads, 0, st>>>(s);
     k_pack_state<<<s.grid_part, kThreads, 0, st>>>(s, pos, vel, img);
+}
+
+void launch_check_finite(const DevSim& s, cudaStream_t st, const double* a, int64_t m) {
+    k_check_finite<<<s.grid_part, kThreads, 0, st>>>(s, a, m);
 }
 
 void launch_unpack_forces(const DevSim& s, cudaStream_t st, double* F, double* u) {

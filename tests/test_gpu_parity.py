@@ -352,6 +352,16 @@ def test_state_round_trip_and_resume():
     twin.set_state(gp, gv, gi)
     tp, tv, ti = twin.get_state()
     assert np.array_equal(tp, gp) and np.array_equal(tv, gv) and np.array_equal(ti, gi)
+    # a non-finite upload is refused (checked on the device) and leaves the state as it was
+    bad_p, bad_v = gp.copy(), gv.copy()
+    bad_p[n // 2, 1] = np.inf
+    bad_v[n // 3, 2] = np.nan
+    for up_p, up_v in ((bad_p, gv), (gp, bad_v)):
+        with pytest.raises(bbmd.BBMDError) as ei:
+            twin.set_state(up_p, up_v, gi)
+        assert ei.value.code == 1
+        tp, tv, ti = twin.get_state()
+        assert np.array_equal(tp, gp) and np.array_equal(tv, gv) and np.array_equal(ti, gi)
     sim.step(30, 0.005)
     twin.step(30, 0.005)
     ap, _, _ = sim.get_state()

@@ -58,7 +58,7 @@ typedef enum {
     BBMD_ERR_BOX_TOO_SMALL = 2,   /* fewer than 3 cells per axis                            */
     BBMD_ERR_OOM = 3,             /* the allocator returned NULL                            */
     BBMD_ERR_CUDA = 4,            /* a CUDA runtime call failed                             */
-    BBMD_ERR_LIST_OVERFLOW = 5,   /* a Verlet list or a staged stencil exceeded capacity    */
+    BBMD_ERR_LIST_OVERFLOW = 5,   /* a staged stencil, or a list beyond 4096, overflowed    */
     BBMD_ERR_NUMERIC = 6,         /* non-finite force or |v| beyond the fixed-point range   */
     BBMD_ERR_TIMEOUT = 7,         /* a bounded device wait gave up                          */
     BBMD_ERR_STATE = 8            /* call not valid in the handle's current state           */
@@ -76,7 +76,12 @@ enum { BBMD_THERMO_NVE = 0, BBMD_THERMO_NH = 1 };
  * skin: Verlet skin (>= 0); the list is rebuilt when some particle has moved more than
  *   skin/2 since the last build (Verlet mode) or, in cell mode, when it has left the
  *   margin skin/2 that the cells carry.
- * list_capacity: maximum list entries per particle (0 = 160; rounded up to 8).
+ * list_capacity: initial list entries per particle (0 = 160; rounded up to 8).  A build
+ *   whose longest list exceeds it keeps going exactly: until the lists are rebuilt, each
+ *   step takes its forces from the cell stencil instead.  The next synchronising call
+ *   (creation, observe, get_state, set_state, get_forces, get_neighbors, ...) grows the
+ *   capacity to the longest list plus an eighth and rebuilds the lists.  Only a list
+ *   longer than 4096 entries is reported, as BBMD_ERR_LIST_OVERFLOW.
  * stencil_capacity: maximum particles staged for one block of cells, i.e. in the
  *   4 x 4 x (block_z + 2) cells around it (0 = from the density, with 15 % headroom).
  * block_z: block shape of the force and list kernels, 2 x 2 x block_z cells per CTA:

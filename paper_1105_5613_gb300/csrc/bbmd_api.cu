@@ -249,7 +249,44 @@ void apply_shape(bbmd_sim* sim, int bz) {
     D.grid_list = (int32_t)(g > 0 ? g : 1);
 }
 
+bbmd_status rebuild_now(bbmd_sim* sim);
+bbmd_status refresh_forces_and_K(bbmd_sim* sim);
+void free_graphs(bbmd_sim* sim);
+
+// A list build cut some lists at the capacity (Verlet mode).  The steps since then took
+// their forces from the cell stencil, which is exact.  Grow the capacity to the longest
+// list seen plus an eighth (at most 4096 entries), rebuild the lists and recompute the
+// forces.  If the cap is reached, the status bit stays and the caller reports the overflow.
+bbmd_status grow_lists(bbmd_sim* sim) {
+    DevSim& D = sim->d;
+    if (D.nbr_mode != BBMD_NBR_VERLET) return BBMD_OK;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        int st = 0, longest = 0;
+        CK(cudaMemcpyAsync(&st, &D.sc->status, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+        CK(cudaMemcpyAsync(&longest, &D.sc->max_len, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+        CK(cudaStreamSynchronize(sim->st));
+        const int cap = D.lcap8 * 8;
+        if (!(st & ST_LIST_OVERFLOW) || (st & ST_STENCIL_OVERFLOW) || cap >= 4096) return BBMD_OK;
+        int want = std::max(longest + longest / 8 + 8, cap + 8);
+        want = std::min(4096, (want + 7) / 8 * 8);
+        uint16_t* grown = (uint16_t*)dev_alloc(sim, (size_t)(want / 8) * (size_t)D.npad * 16);
+        if (!grown) return fail(sim, BBMD_ERR_OOM, "growing the Verlet lists");
+        dev_free(sim, D.list);
+        D.list = grown;
+        D.lcap8 = want / 8;
+        free_graphs(sim);  // the captured kernels hold the old list
+        const int cleared = st & ~ST_LIST_OVERFLOW;
+        CK(cudaMemcpyAsync(&D.sc->status, &cleared, sizeof(int), cudaMemcpyHostToDevice, sim->st));
+        CK(cudaStreamSynchronize(sim->st));  // `cleared` lives on this stack frame
+        rebuild_now(sim);
+        refresh_forces_and_K(sim);
+    }
+    return BBMD_OK;
+}
+
 bbmd_status read_status(bbmd_sim* sim) {
+    bbmd_status g = grow_lists(sim);
+    if (g != BBMD_OK) return g;
     int st = 0;
     CK(cudaMemcpyAsync(&st, &sim->d.sc->status, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
     CK(cudaStreamSynchronize(sim->st));
@@ -584,6 +621,7 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     dev_free(sim, tpos);
     dev_free(sim, tvel);
     if (rc == BBMD_OK) rc = rebuild_now(sim);
+    if (rc == BBMD_OK) rc = grow_lists(sim);  // lists longer than the capacity asked for
     if (rc == BBMD_OK && sim->shapes.size() > 1) rc = autotune_shape(sim);
     if (rc == BBMD_OK) rc = refresh_forces_and_K(sim);
     if (rc == BBMD_OK) rc = read_status(sim);
@@ -954,6 +992,10 @@ bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int
                                int64_t* nbr, int64_t cap) {
     if (!sim || !offsets) return BBMD_ERR_ARG;
     if (sim->d.nbr_mode != BBMD_NBR_VERLET) return fail(sim, BBMD_ERR_STATE, "no stored list in cell mode");
+    {
+        const bbmd_status g = read_status(sim);  // grows cut lists first
+        if (g != BBMD_OK) return g;
+    }
     const int64_t n = sim->d.n;
     if (!ids) m = n;
     if (m < 0 || m > n) return fail(sim, BBMD_ERR_ARG, "m");

@@ -54,6 +54,9 @@ struct DevScalars {
     int near;                // 1: some displacement of this step exceeds half the threshold
     int status;              // ST_* bits
     int bad_input;           // set_state: 1 if an uploaded value is not finite
+    int list_short;          // 1: the stored lists were cut at the capacity; the forces come
+                             //    from the cell stencil until the lists are rebuilt larger
+    int max_len;             // longest cut list of the last build (entries)
 };
 
 struct PairTab {

@@ -577,9 +577,19 @@ __device__ __forceinline__ float keep_reach(const float* hi4, int sj) {
     return fmaxf(hi4[sj], hi4[2 + sj]) * (1.0f + 0x1p-9f);
 }
 
+// Which force kernel runs: in cell mode the stencil kernel (MODE 1); in Verlet mode the
+// list kernel (MODE 0), or the stencil kernel while the stored lists are cut at the
+// capacity (exact forces until the host has grown the lists).
+template <int MODE>
+__device__ __forceinline__ bool force_selected(const DevSim& s) {
+    if (s.nbr_mode != BBMD_NBR_VERLET) return MODE == 1;
+    return (s.sc->list_short != 0) == (MODE == 1);
+}
+
 // MODE 0: Verlet list.  MODE 1: every particle of the 27-cell stencil (no stored list).
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
 __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
+    if (!force_selected<MODE>(s)) return;  // CTA-uniform, before any barrier
     extern __shared__ float4 smem[];
     __shared__ Region R[kStageBuffers];
     __shared__ __align__(8) uint64_t mbar[kStageBuffers];
@@ -967,7 +977,12 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                     __syncwarp();
                 }
                 if (len > lcap) {
+                    // the list is cut: flagged for the host (which grows the capacity at its
+                    // next synchronising call) and, until then, the forces come from the
+                    // cell stencil
                     set_status(s, ST_LIST_OVERFLOW);
+                    s.sc->list_short = 1;
+                    atomicMax(&s.sc->max_len, len);
                     len = lcap;
                 }
                 if (act && (len & 1)) {
@@ -1078,6 +1093,7 @@ __device__ __forceinline__ void pair_fp64(const DevSim& s, int si, const Pos64& 
 
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
 __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
+    if (!force_selected<MODE>(s)) return;  // CTA-uniform, before any barrier
     extern __shared__ float4 smem[];
     __shared__ Region R;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1323,12 +1339,12 @@ int list_blocks_per_sm(const DevSim& s) {
     return nb > 0 ? nb : 1;
 }
 
+// Verlet mode launches the list kernel and, behind it, the stencil kernel: exactly one of
+// the two runs, by the device flag of cut lists.
 void launch_force(const DevSim& s, cudaStream_t st, bool energy, bool ke) {
     bool fs = s.pt.shift == BBMD_SHIFT_FORCE;
-    if (s.nbr_mode == BBMD_NBR_VERLET)
-        run_force_mode<0>(s, st, energy, ke, fs);
-    else
-        run_force_mode<1>(s, st, energy, ke, fs);
+    if (s.nbr_mode == BBMD_NBR_VERLET) run_force_mode<0>(s, st, energy, ke, fs);
+    run_force_mode<1>(s, st, energy, ke, fs);
 }
 
 void launch_force_many(const ManySims& m, int total, bool fp64, bool cell, bool ke, bool fshift,
@@ -1342,12 +1358,23 @@ void launch_force_many(const ManySims& m, int total, bool fp64, bool cell, bool 
             else run_force_many<1, false, false>(m, total, fp64, smax_max, st);
         }
     } else {
+        // list kernel, then the stencil kernel that stands in for replicas with cut lists
         if (ke) {
-            if (fshift) run_force_many<0, true, true>(m, total, fp64, smax_max, st);
-            else run_force_many<0, true, false>(m, total, fp64, smax_max, st);
+            if (fshift) {
+                run_force_many<0, true, true>(m, total, fp64, smax_max, st);
+                run_force_many<1, true, true>(m, total, fp64, smax_max, st);
+            } else {
+                run_force_many<0, true, false>(m, total, fp64, smax_max, st);
+                run_force_many<1, true, false>(m, total, fp64, smax_max, st);
+            }
         } else {
-            if (fshift) run_force_many<0, false, true>(m, total, fp64, smax_max, st);
-            else run_force_many<0, false, false>(m, total, fp64, smax_max, st);
+            if (fshift) {
+                run_force_many<0, false, true>(m, total, fp64, smax_max, st);
+                run_force_many<1, false, true>(m, total, fp64, smax_max, st);
+            } else {
+                run_force_many<0, false, false>(m, total, fp64, smax_max, st);
+                run_force_many<1, false, false>(m, total, fp64, smax_max, st);
+            }
         }
     }
 }

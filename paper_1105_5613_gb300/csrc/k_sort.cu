@@ -26,6 +26,10 @@ __host__ __device__ __forceinline__ int scan_chunks(const DevSim& s) {
 
 __device__ __forceinline__ void zero_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
+    if (lb == 0 && threadIdx.x == 0) {  // the list build of this rebuild sets them afresh
+        s.sc->list_short = 0;
+        s.sc->max_len = 0;
+    }
     for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c <= s.ncell;
          c += (int64_t)lg * blockDim.x) {
         s.count[c] = 0;

@@ -24,11 +24,11 @@ def _lib():
     bbmd.load()
 
 
-def lattice_replicas(ms, temps, shake=0.05):
+def lattice_replicas(ms, temps, shake=0.05, rho=1.2):
     ns, boxes, pos, vel, sp = [], [], [], [], []
     for r, (m, T) in enumerate(zip(ms, temps)):
         n = 4 * m ** 3
-        L = gen.box_for(n, 1.2)
+        L = gen.box_for(n, rho)
         rng = np.random.default_rng(100 + r)
         pos.append((gen.fcc_lattice(m, L) + rng.uniform(-shake, shake, (n, 3))) % L)
         vel.append(gen.maxwell_boltzmann(n, T, r, np.ones(n)))
@@ -38,11 +38,18 @@ def lattice_replicas(ms, temps, shake=0.05):
     return ns, boxes, pos, vel, sp
 
 
-@pytest.mark.parametrize("prec,mode,tol", [(0, 0, 1e-4), (1, 0, 1e-9), (0, 1, 1e-4)])
-def test_batch_replicas_match_oracle(prec, mode, tol):
+@pytest.mark.parametrize("prec,mode,tol,lcap", [(0, 0, 1e-4, 0), (1, 0, 1e-9, 0), (0, 1, 1e-4, 0),
+                                                (0, 0, 1e-4, 88), (1, 0, 1e-9, 88)])
+def test_batch_replicas_match_oracle(prec, mode, tol, lcap):
+    # lcap 88 holds the lists of the lattice at rho = 1.19 (86 at most: its seventh shell
+    # lies just beyond rc + skin) but not those of the liquid: the replicas' lists are cut
+    # during the run and their forces come from the cell stencil
     ms, temps = [8, 9, 10, 11], [0.5, 1.0, 1.5, 2.0]
-    ns, boxes, pos, vel, sp = lattice_replicas(ms, temps)
-    p = bbmd.ka_params(precision=prec, nbr_mode=mode)
+    if lcap:
+        ns, boxes, pos, vel, sp = lattice_replicas(ms, temps, shake=0.0, rho=1.19)
+    else:
+        ns, boxes, pos, vel, sp = lattice_replicas(ms, temps)
+    p = bbmd.ka_params(precision=prec, nbr_mode=mode, list_capacity=lcap)
     b = bbmd.Batch(p, ns, boxes, sp, pos, vel)
     th = [(bbmd.THERMO_NH, T, T, 0.5) for T in temps]
     b.step(100, 0.005, th)

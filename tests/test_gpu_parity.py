@@ -311,9 +311,6 @@ def test_errors_are_reported():
     with pytest.raises(bbmd.BBMDError) as ei:
         bbmd.Sim(bbmd.ka_params(), n, L, sp, p2, vel)
     assert ei.value.code == 1
-    with pytest.raises(bbmd.BBMDError) as ei:  # list capacity far too small
-        bbmd.Sim(bbmd.ka_params(list_capacity=16), n, L, sp, pos, vel)
-    assert ei.value.code == 5
     # staged capacity far below one block region, in every shape, precision and mode: the
     # kernels take only the staged particles and the overflow is reported
     for prec in (bbmd.PREC_MIXED, bbmd.PREC_FP64):
@@ -328,6 +325,58 @@ def test_errors_are_reported():
     with pytest.raises(bbmd.BBMDError):
         sim.observe(bbmd.OBS_MSD)  # no reference yet
     sim.step(5, 0.005)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lists_grow_beyond_the_capacity(prec):
+    """A list capacity far below the lists: creation grows it to the longest list and the
+    lists and forces are those of the oracle."""
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.12, list_capacity=16, precision=prec)
+    assert sim.info()["list_capacity"] >= 100
+    xq, xfix, k = quantized(pos, L)
+    off, nbr = sim.get_neighbors()
+    offo, nbro = oracle.neighbors(xfix, sp, L, k, oracle.list_R2(oracle_params(p), 0.3),
+                                  "cells", rcell=2.8)
+    assert np.array_equal(off, offo) and np.array_equal(nbr, nbro)
+    Fo = oracle.forces(xq, sp, L, oracle_params(p))[0]
+    F = sim.get_forces()
+    if prec == 1:
+        rel = np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), 1e-3)
+        assert rel.max() <= 1e-10
+    else:
+        e = force_errors(F, Fo)
+        assert np.median(e) <= 1e-5 and e.max() <= 1e-4
+    sim.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-4), (1, 1e-9)])
+def test_cut_lists_fall_back_to_the_stencil(prec, tol):
+    """At rho = 1.19 the lattice's seventh shell lies just beyond rc + skin, so its lists
+    hold 86 entries at most, against up to about 115 in the liquid it melts into.  With a
+    capacity of 88 the rebuilds of the run cut lists, and the steps take their forces
+    from the cell stencil instead.  The trajectory still follows the oracle, and the next
+    synchronising call grows the lists."""
+    n = 4 * 10 ** 3
+    L = gen.box_for(n, 1.19)
+    pos = gen.fcc_lattice(10, L)
+    sp = gen.assign_species(n, n // 5, 0)
+    vel = gen.maxwell_boltzmann(n, 2.0, 0, np.ones(n))
+    p = bbmd.ka_params(precision=prec, list_capacity=88)
+    sim = bbmd.Sim(p, n, L, sp, pos, vel)
+    assert sim.info()["list_capacity"] == 88
+    xq, _, _ = quantized(pos, L)
+    st = oracle.MDState(xq, vel, sp, L, oracle_params(p))
+    oracle.md_run(st, 100, 0.005, use_cells=True)
+    sim.step(100, 0.005)
+    gp, gv, _ = sim.get_state()
+    assert min_image_rms(gp, st.pos, L) <= tol
+    assert np.sqrt(((gv - st.vel) ** 2).sum(1).mean()) <= 50 * tol
+    assert sim.info()["list_capacity"] > 88
+    oracle.md_run(st, 20, 0.005, use_cells=True)
+    sim.step(20, 0.005)
+    gp, _, _ = sim.get_state()
+    assert min_image_rms(gp, st.pos, L) <= tol
     sim.close()
 
 

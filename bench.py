@@ -367,7 +367,8 @@ def run_ours(args):
                      "frac": achieved / fp32_peak, "traffic": traffic,
                      "algorithmic": f"{hp_per:.2f} half pairs/particle x {FLOP_PER_HALF_PAIR:.0f} "
                                     f"flop x {n} particles per launch",
-                     "force_ms": force_ms},
+                     "force_ms": force_ms,
+                     "issue": force_issue(n, force_ms, block_z, clock_mhz)},
         "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
         "block_z": block_z,
         "rebuilds_per_step": nreb / nprof,
@@ -483,9 +484,10 @@ def ctypes_sizeof_obs(bbmd):
     return ctypes.sizeof(bbmd.bbmd_obs)
 
 
-def force_traffic(n):
-    """DRAM bytes (read + write) per k_force launch from the committed ncu summary, scaled to
-    n particles; None when the kernel source changed since those counters were taken."""
+def force_counters():
+    """The committed ncu record of one list-mode k_force launch (DRAM bytes and warp
+    instructions per particle, block shape), or None when the kernel source changed since
+    those counters were taken."""
     import hashlib
 
     tf = os.path.join(ROOT, "profiles", "force_traffic.json")
@@ -493,11 +495,28 @@ def force_traffic(n):
     try:
         rec = json.load(open(tf))
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        if rec.get("k_force_cu_sha1") != sha:
-            return None
-        return rec["bytes_per_particle"] * n
+        return rec if rec.get("k_force_cu_sha1") == sha else None
     except Exception:
         return None
+
+
+def force_traffic(n):
+    """DRAM bytes (read + write) per k_force launch, scaled to n particles (every array the
+    kernel touches is per particle), or None."""
+    rec = force_counters()
+    return rec["bytes_per_particle"] * n if rec else None
+
+
+def force_issue(n, force_ms, block_z, clock_mhz):
+    """Issue-slot view of the same launch: warp instructions (from the ncu record, same
+    block shape) per second against 4 warp instructions per SM per cycle."""
+    rec = force_counters()
+    if not rec or rec.get("block_z") != block_z or "warp_inst_per_particle" not in rec:
+        return None
+    peak = SM_COUNT * 4 * clock_mhz * 1e6
+    rate = rec["warp_inst_per_particle"] * n / (force_ms / 1e3)
+    return {"warp_inst_per_s": rate, "peak": peak, "frac": rate / peak,
+            "warp_inst_per_particle": rec["warp_inst_per_particle"]}
 
 
 def cpu_sample_state(ncell=40, seed=0):

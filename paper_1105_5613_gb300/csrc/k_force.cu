@@ -821,9 +821,9 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
 // broadcast shared-memory reads: the sign of r^2 - R2lo(species of j) is shifted into a
 // 32-bit word (candidate u lands in bit 31 - u) and the smallest |r^2 - R2lo| of the word
 // is kept.  Only a word whose minimum falls inside the band goes through the exact rule,
-// candidate by candidate.  The set bits of up to kRingWords words are then written as
-// list offsets, two entries per 32-bit store into [kb][npad][8] uint16, at a row pointer
-// advanced once per four pairs.
+// candidate by candidate.  The set bits of each word are then written as list offsets,
+// two entries per 32-bit store into [kb][npad][8] uint16, at a row pointer advanced once
+// per four pairs.
 
 __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
@@ -889,65 +889,61 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                     }
                     __syncwarp();
                     const int nw = min(kRingWords, (fill - done + 31) >> 5);
-                    unsigned m[kRingWords];
-#pragma unroll
-                    for (int q = 0; q < kRingWords; ++q) {
+                    // bitmask of the candidates of ring word cq (stream position, a
+                    // multiple of 32) that enter this particle's list
+                    auto test_word = [&](int cq) -> unsigned {
                         unsigned inw = 0u;
-                        const int cq = done + 32 * q;
-                        if (q < nw) {  // warp-uniform
-                            const uint4* ip = reinterpret_cast<const uint4*>(ring + (cq & (kRing - 1)));
-                            float near = far;
+                        const uint4* ip = reinterpret_cast<const uint4*>(ring + (cq & (kRing - 1)));
+                        float near = far;
 #pragma unroll
-                            for (int v = 0; v < 8; ++v) {
-                                const uint4 iv = ip[v];
-                                const uint32_t ix[4] = {iv.x, iv.y, iv.z, iv.w};
+                        for (int v = 0; v < 8; ++v) {
+                            const uint4 iv = ip[v];
+                            const uint32_t ix[4] = {iv.x, iv.y, iv.z, iv.w};
 #pragma unroll
-                                for (int h = 0; h < 4; ++h) {
-                                    const float4 p = sm[ix[h]];
-                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                    // r^2 - R2lo(species of j), one FMA chain; sign = inside
-                                    const float dlo = fmaf(dz, dz,
-                                                           fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
-                                    inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
-                                    near = fminf(near, fabsf(dlo));
-                                }
-                            }
-                            const int nv = fill - cq;
-                            unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
-                            if (cself >= cq && cself < cq + 32) valid &= ~(0x80000000u >> (cself - cq));
-                            if (!act) valid = 0u;
-                            inw &= valid;
-                            const bool chk = near < band && valid != 0u;
-                            if (__any_sync(FULL, chk) && chk) {
-                                // the same FP32 value decides which candidates are in the
-                                // band; those are decided by the exact rule
-                                unsigned bw = valid;
-                                while (bw) {
-                                    const int u = __clz(bw);
-                                    bw &= 0x7fffffffu >> u;
-                                    const int t = (int)ring[(cq + u) & (kRing - 1)];
-                                    const float4 p = sm[t];
-                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                    const float dlo = fmaf(dz, dz,
-                                                           fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
-                                    if (!(fabsf(dlo) < band)) continue;
-                                    const unsigned bit = 0x80000000u >> u;
-                                    inw &= ~bit;
-                                    if (!min_image_copy(s, dx, dy, dz)) continue;
-                                    const int tj = p.w != 0.f ? 1 : 0;
-                                    const int64_t gj = staged_global(Rc, t);
-                                    if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= bit;
-                                }
+                            for (int h = 0; h < 4; ++h) {
+                                const float4 p = sm[ix[h]];
+                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                // r^2 - R2lo(species of j), one FMA chain; sign = inside
+                                const float dlo = fmaf(dz, dz,
+                                                       fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
+                                inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
+                                near = fminf(near, fabsf(dlo));
                             }
                         }
-                        m[q] = inw;
-                    }
-#pragma unroll
-                    for (int q = 0; q < kRingWords; ++q) {
-                        unsigned bits = m[q];
+                        const int nv = fill - cq;
+                        unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
+                        if (cself >= cq && cself < cq + 32) valid &= ~(0x80000000u >> (cself - cq));
+                        if (!act) valid = 0u;
+                        inw &= valid;
+                        const bool chk = near < band && valid != 0u;
+                        if (__any_sync(FULL, chk) && chk) {
+                            // the same FP32 value decides which candidates are in the band;
+                            // those are decided by the exact rule
+                            unsigned bw = valid;
+                            while (bw) {
+                                const int u = __clz(bw);
+                                bw &= 0x7fffffffu >> u;
+                                const int t = (int)ring[(cq + u) & (kRing - 1)];
+                                const float4 p = sm[t];
+                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                const float dlo = fmaf(dz, dz,
+                                                       fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
+                                if (!(fabsf(dlo) < band)) continue;
+                                const unsigned bit = 0x80000000u >> u;
+                                inw &= ~bit;
+                                if (!min_image_copy(s, dx, dy, dz)) continue;
+                                const int tj = p.w != 0.f ? 1 : 0;
+                                const int64_t gj = staged_global(Rc, t);
+                                if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= bit;
+                            }
+                        }
+                        return inw;
+                    };
+                    // the set bits of word cq as list entries, in candidate order
+                    auto append_word = [&](int cq, unsigned bits) {
                         // the word's 32 ring entries are contiguous (word starts are
                         // multiples of 32 in a ring of 256)
-                        const uint32_t* const rw = ring + ((done + 32 * q) & (kRing - 1));
+                        const uint32_t* const rw = ring + (cq & (kRing - 1));
                         // entries go out in pairs (one 32-bit store each at the running row
                         // pointer; entries beyond the capacity are counted, not stored): a
                         // pending odd entry is completed by the word's first bit, then two
@@ -972,7 +968,12 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                             put_pair(t1 | (rw[u2] << 16));
                             len += 2;
                         }
-                    }
+                    };
+                    // one word at a time, the loop kept rolled: testing all words before
+                    // appending, unrolled, made a kernel large enough to stall on
+                    // instruction fetch (6-11 % slower)
+#pragma unroll 1
+                    for (int q = 0; q < nw; ++q) append_word(done + 32 * q, test_word(done + 32 * q));
                     done += 32 * nw;
                     __syncwarp();
                 }

@@ -278,6 +278,9 @@ __device__ bool finish_block(const DevSim& s, const Region& R, float4* sm, uint6
     return true;
 }
 
+#ifndef BBMD_CELL_PAIRWORDS
+#define BBMD_CELL_PAIRWORDS 1
+#endif
 #ifndef BBMD_STAGE_BUFFERS
 #define BBMD_STAGE_BUFFERS 1  // 2: stage block i+1 while block i is computed
 #endif
@@ -716,8 +719,9 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                         }
                         __syncwarp();
                         const int nw = min(kRingWords, (fill - done + 31) >> 5);
-                        for (int q = 0; q < nw; ++q) {
-                            const int cq = done + 32 * q;
+                        // bitmask of the candidates of ring word cq (a multiple of 32)
+                        // inside the cutoff
+                        auto filter_word = [&](int cq) -> unsigned {
                             const uint4* ip = reinterpret_cast<const uint4*>(ring + (cq & (kRing - 1)));
                             unsigned inw = 0u;
                             float near = far;
@@ -760,6 +764,32 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                                     if (r2_exact(s, gi, gj) < s.pt.rc2[si * 2 + tj]) inw |= bit;
                                 }
                             }
+                            return inw;
+                        };
+#if BBMD_CELL_PAIRWORDS
+                        // the forces of two words' set bits in one loop: the warp runs to the
+                        // largest count of the pair rather than to each word's largest; a
+                        // flush's words lie in one half of the ring, so the two words' 64
+                        // entries are contiguous
+                        for (int q = 0; q < nw; q += 2) {
+                            const int cq = done + 32 * q;
+                            const unsigned w0 = filter_word(cq);
+                            const unsigned w1 = q + 1 < nw ? filter_word(cq + 32) : 0u;
+                            unsigned long long bits = ((unsigned long long)w0 << 32) | w1;
+                            const uint32_t* const rw = ring + (cq & (kRing - 1));
+                            while (bits) {
+                                const int u = __clzll(bits);
+                                bits &= 0x7fffffffffffffffull >> u;
+                                const float4 p = sm[rw[u]];
+                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
+                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                pair_add<ENERGY, FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
+                            }
+                        }
+#else
+                        for (int q = 0; q < nw; ++q) {
+                            const int cq = done + 32 * q;
+                            unsigned inw = filter_word(cq);
                             while (inw) {
                                 const int u = __clz(inw);
                                 inw &= 0x7fffffffu >> u;
@@ -769,6 +799,7 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                                 pair_add<ENERGY, FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
                             }
                         }
+#endif
                         done += 32 * nw;
                         __syncwarp();
                     }

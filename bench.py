@@ -21,6 +21,7 @@ import argparse
 import json
 import math
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -102,14 +103,19 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms into a temporary file
+    (copied to `keep` when given, e.g. as evidence beside a profile)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, path, gpu=None):
-        self.path = path
+    def __init__(self, keep=None, gpu=None):
+        import tempfile
+
+        fd, self.path = tempfile.mkstemp(prefix="bbmd_clocks_", suffix=".csv")
+        os.close(fd)
+        self.keep = keep
         self.gpu = gpu  # nvidia-smi index of this rank's GPU (None: every GPU)
         self.proc = None
 
@@ -132,10 +138,16 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.f.close()
+        if self.keep:
+            try:
+                shutil.copyfile(self.path, self.keep)
+            except OSError:
+                pass
 
     def summary(self):
         try:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r]
+            os.unlink(self.path)
         except Exception:
             rows = []
         sm, mx, reasons = [], None, set()
@@ -229,9 +241,8 @@ def run_ours(args):
     # ---- device-timed region ----
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     local_gpu = torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else None
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else os.devnull,
-                       gpu=local_gpu)
+    keep = os.environ.get("BBMD_CLOCKS_CSV")  # optional copy of the raw samples
+    clk = ClockSampler(f"{keep}.rank{rank}" if keep else None, gpu=local_gpu)
     barrier()
     torch.cuda.synchronize()
     with clk:

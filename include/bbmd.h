@@ -21,8 +21,10 @@
  *     bbmd_step returns after enqueueing; every call that returns host data synchronises
  *     that stream.
  *   - Errors are returned as bbmd_status codes, never by abort or exit.  A device-side
- *     status word (list overflow, non-finite force, velocity overflow) is sticky and is
- *     reported by the next synchronising call.  bbmd_last_error gives a message.
+ *     status word (staged-stencil overflow, a list beyond 4096 entries, non-finite force,
+ *     velocity overflow, a bounded wait that gave up) is sticky and is reported by the
+ *     next synchronising call; lists longer than their capacity are grown there instead
+ *     (see list_capacity).  bbmd_last_error gives a message.
  *   - A handle is not thread-safe.
  *
  * State representation (the exact rules the test oracle implements independently)

@@ -1,0 +1,59 @@
+"""Host logic of bench.py on CPU: the clock-sample summary (median SM clock, throttle
+reasons) and the ncu counter record of the force kernel, which is used only while the
+kernel source it was taken on is unchanged."""
+import hashlib
+import json
+import os
+
+import pytest
+
+
+@pytest.fixture()
+def bench():
+    import bench as b
+
+    return b
+
+
+def test_clock_summary_median_and_reasons(bench, tmp_path):
+    c = bench.ClockSampler()
+    rows = ["0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1380.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "garbage line"]
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    assert not os.path.exists(c.path)  # the temporary file is removed once read
+
+
+def test_clock_summary_without_samples(bench):
+    c = bench.ClockSampler()
+    assert c.summary() is None
+
+
+def _fake_tree(root, src_text, rec):
+    (root / "profiles").mkdir()
+    csrc = root / "paper_1105_5613_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k_force.cu").write_text(src_text)
+    (root / "profiles" / "force_traffic.json").write_text(json.dumps(rec))
+
+
+def test_force_counters_follow_the_source(bench, tmp_path, monkeypatch):
+    src = "// kernel source\n"
+    rec = {"block_z": 4, "bytes_per_particle": 284.0, "warp_inst_per_particle": 150.0,
+           "k_force_cu_sha1": hashlib.sha1(src.encode()).hexdigest()}
+    _fake_tree(tmp_path, src, rec)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.force_traffic(1000) == pytest.approx(284000.0)
+    issue = bench.force_issue(1_000_000, 1.0, 4, 2000.0)
+    # 150e6 warp instructions in 1 ms against 152 SMs x 4 per cycle at 2 GHz
+    assert issue["frac"] == pytest.approx(1.5e11 / (152 * 4 * 2e9))
+    assert bench.force_issue(1_000_000, 1.0, 8, 2000.0) is None  # another block shape
+    # any change of the source voids the record
+    (tmp_path / "paper_1105_5613_gb300" / "csrc" / "k_force.cu").write_text(src + " ")
+    assert bench.force_traffic(1000) is None
+    assert bench.force_issue(1_000_000, 1.0, 4, 2000.0) is None

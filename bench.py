@@ -110,10 +110,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, keep=None, gpu=None):
+    def __init__(self, keep=None, gpu=None, tmpdir=None):
         import tempfile
 
-        fd, self.path = tempfile.mkstemp(prefix="bbmd_clocks_", suffix=".csv")
+        fd, self.path = tempfile.mkstemp(prefix="bbmd_clocks_", suffix=".csv", dir=tmpdir)
         os.close(fd)
         self.keep = keep
         self.gpu = gpu  # nvidia-smi index of this rank's GPU (None: every GPU)

@@ -8,6 +8,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+@pytest.hookimpl(tryfirst=True)
 def pytest_configure(config):
+    # temporary test files stay inside the checkout (an ignored folder)
+    if getattr(config.option, "basetemp", None) is None:
+        work = os.path.join(ROOT, "_work")
+        os.makedirs(work, exist_ok=True)
+        config.option.basetemp = os.path.join(work, "pytest_tmp")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running statistical check")

@@ -16,7 +16,7 @@ def bench():
 
 
 def test_clock_summary_median_and_reasons(bench, tmp_path):
-    c = bench.ClockSampler()
+    c = bench.ClockSampler(tmpdir=str(tmp_path))
     rows = ["0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
             "0, 2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
             "0, 2070, 2070, 1380.0, 0x4, Not Active, Not Active, Not Active, Active",
@@ -29,8 +29,8 @@ def test_clock_summary_median_and_reasons(bench, tmp_path):
     assert not os.path.exists(c.path)  # the temporary file is removed once read
 
 
-def test_clock_summary_without_samples(bench):
-    c = bench.ClockSampler()
+def test_clock_summary_without_samples(bench, tmp_path):
+    c = bench.ClockSampler(tmpdir=str(tmp_path))
     assert c.summary() is None
 
 

@@ -10,10 +10,8 @@ if ROOT not in sys.path:
 
 @pytest.hookimpl(tryfirst=True)
 def pytest_configure(config):
-    # temporary test files stay inside the checkout (an ignored folder)
+    # temporary test files stay inside the checkout, in an ignored folder
     if getattr(config.option, "basetemp", None) is None:
-        work = os.path.join(ROOT, "_work")
-        os.makedirs(work, exist_ok=True)
-        config.option.basetemp = os.path.join(work, "pytest_tmp")
+        config.option.basetemp = os.path.join(ROOT, ".pytest_tmp")
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running statistical check")

@@ -412,6 +412,35 @@ def test_gr_counts_against_pdist():
     _ = spatial
 
 
+def test_gr_normalisation_of_single_pairs():
+    """A lone pair at a known distance: its bin holds the two ordered pairs, and g there
+    is the box volume over the shell volume times the species counts of the definition
+    (N_a N_b for a != b, N_a (N_a - 1) for a = b).  Swapping N_b - 1 for N_b, or the shell
+    volume for a slab, changes the value by a factor."""
+    L, rmax, nb = 20.0, 5.0, 50
+    dr = rmax / nb
+    r0 = 2.345
+    q = int(r0 / dr)
+    shell = 4.0 * math.pi / 3.0 * ((q + 1) ** 3 - q ** 3) * dr ** 3
+    V = L ** 3
+    far = [15.0, 15.0, 15.0]  # farther than rmax from the pair (minimum image)
+    # two B particles and one distant A: N_B = 2, N_B' = 1
+    pos = np.array([[2.0, 2.0, 2.0], [2.0 + r0, 2.0, 2.0], far])
+    sp = np.array([1, 1, 0], dtype=np.uint8)
+    xfix, k = oracle.quantize(pos, L)
+    cnt = oracle.gr_counts(xfix, sp, L, k, nb, rmax)
+    assert cnt[1, 1, q] == 2 and cnt.sum() == 2
+    g = oracle.gr_normalize(cnt, sp, L, rmax)
+    assert g[1, 1, q] == pytest.approx(V * 2 / (2 * 1 * shell), rel=1e-12)
+    # one A and one B at r0, one distant B: N_A = 1, N_B = 2
+    sp = np.array([0, 1, 1], dtype=np.uint8)
+    cnt = oracle.gr_counts(xfix, sp, L, k, nb, rmax)
+    assert cnt[0, 1, q] == 1 and cnt[1, 0, q] == 1 and cnt.sum() == 2
+    g = oracle.gr_normalize(cnt, sp, L, rmax)
+    assert g[0, 1, q] == pytest.approx(V * 1 / (1 * 2 * shell), rel=1e-12)
+    assert g[1, 0, q] == pytest.approx(V * 1 / (2 * 1 * shell), rel=1e-12)
+
+
 def test_msd_fs_closed_forms():
     pos, _, sp, L = liquid(ncell=3, seed=15)
     im = np.zeros(pos.shape, dtype=np.int32)
@@ -424,6 +453,23 @@ def test_msd_fs_closed_forms():
     msd, fs = oracle.msd_fs(moved, im2, pos, im, sp, L, kvec=7.25)
     assert np.allclose(msd, (dvec ** 2).sum(), rtol=1e-12)
     assert np.allclose(fs, np.cos(7.25 * dvec).mean(), rtol=1e-10)
+
+
+def test_msd_fs_per_species_and_through_many_boxes():
+    """Species A and B moved by different vectors, B by more than a box length: each
+    species' MSD and F_s is its own vector's closed form, so a species mix-up, a dropped
+    image counter or a wrong average fails here."""
+    pos, _, sp, L = liquid(ncell=3, seed=21)
+    im = np.zeros(pos.shape, dtype=np.int32)
+    d = {0: np.array([0.25, 0.5, -0.125]), 1: np.array([-1.5 * L, 0.75, 2.25 * L])}
+    moved = pos + np.where((sp == 1)[:, None], d[1], d[0])
+    im2 = np.floor(moved / L).astype(np.int32)
+    moved = moved - L * im2
+    k = 7.25
+    msd, fs = oracle.msd_fs(moved, im2, pos, im, sp, L, kvec=k)
+    for a in (0, 1):
+        assert msd[a] == pytest.approx((d[a] ** 2).sum(), rel=1e-12)
+        assert fs[a] == pytest.approx(np.cos(k * d[a]).mean(), rel=1e-9, abs=1e-12)
 
 
 @pytest.mark.parametrize("method", ["brute", "cells", "cells_full"])

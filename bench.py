@@ -299,8 +299,7 @@ def run_ours(args):
     sim.close()
 
     # ---- FP64 form on the same workload (a few steps) ----
-    fp64 = None
-    if not args.no_fp64:
+    def leg_fp64():
         p64 = bbmd.ka_params(precision=bbmd.PREC_FP64)
         sim64 = bbmd.Sim(p64, n, L, sp, None, None, T0=T_HIGH, seed=rank,
                          stream=stream.cuda_stream, use_torch_allocator=True)
@@ -315,13 +314,14 @@ def run_ours(args):
         ms64 = a0.elapsed_time(a1)
         ph64, _ = sim64.step_profiled(1, DT, therm(1))
         sim64.close()
-        fp64 = {"value": n * k64 / (ms64 / 1e3), "unit": "particle-steps/s", "steps": k64,
+        return {"value": n * k64 / (ms64 / 1e3), "unit": "particle-steps/s", "steps": k64,
                 "ms_per_step": ms64 / k64, "force_ms": ph64["force"]}
+
+    fp64 = None if args.no_fp64 else optional_leg(leg_fp64)
 
     # ---- soft-sphere mixture with the shifted-force truncation (Eqs. sc0, mod0), the paper's
     # own benchmark potential, on the same N: melted at T=2.0, then timed at T=0.5 ----
-    soft = None
-    if args.soft_steps > 0:
+    def leg_soft():
         ps = bbmd.ka_params(potential=bbmd.POT_SOFT, shift=bbmd.SHIFT_FORCE)
         sims = bbmd.Sim(ps, n, L, sp, None, None, T0=T_HIGH, seed=rank,
                         stream=stream.cuda_stream, use_torch_allocator=True)
@@ -335,16 +335,20 @@ def run_ours(args):
         s1.record(stream)
         s1.synchronize()
         mss = s0.elapsed_time(s1)
-        soft = {"workload": f"soft-sphere mixture (Eq. sc0) with shifted-force truncation "
-                            f"(Eq. mod0), rc = 2.5 sigma_ab, N={n}, rho=1.2, Nose-Hoover T=0.5 "
-                            "after melting at T=2.0",
-                "value": n * args.soft_steps / (mss / 1e3), "unit": "particle-steps/s",
-                "steps": args.soft_steps, "ms_per_step": mss / args.soft_steps,
-                "block_z": sims.info()["block_z"],
-                "T": sims.observe(bbmd.OBS_ENERGY)["temperature"]}
+        out = {"workload": f"soft-sphere mixture (Eq. sc0) with shifted-force truncation "
+                           f"(Eq. mod0), rc = 2.5 sigma_ab, N={n}, rho=1.2, Nose-Hoover T=0.5 "
+                           "after melting at T=2.0",
+               "value": n * args.soft_steps / (mss / 1e3), "unit": "particle-steps/s",
+               "steps": args.soft_steps, "ms_per_step": mss / args.soft_steps,
+               "block_z": sims.info()["block_z"],
+               "T": sims.observe(bbmd.OBS_ENERGY)["temperature"]}
         sims.close()
-    replicas = run_replicas(args, stream) if args.replicas > 0 else None
-    large = run_large(args, stream) if args.large_steps > 0 or args.large_fp64_steps > 0 else None
+        return out
+
+    soft = optional_leg(leg_soft) if args.soft_steps > 0 else None
+    replicas = optional_leg(run_replicas, args, stream) if args.replicas > 0 else None
+    large = (optional_leg(run_large, args, stream)
+             if args.large_steps > 0 or args.large_fp64_steps > 0 else None)
     if rank != 0:
         return None
     value = whole_job_rate(n * args.steps, ws, ms)
@@ -395,8 +399,24 @@ def run_ours(args):
         "observables": {"T": obs["temperature"], "pe_per_particle": obs["pe"] / n},
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        out["cpu_baseline"] = optional_leg(cpu_baseline, args.cpu_seconds)
     return out
+
+
+def optional_leg(fn, *a):
+    """Run one secondary leg of the bench; a failure is reported in its place (an "error"
+    entry) instead of ending the run, so the headline line is printed either way."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - any failure of a secondary leg
+        try:
+            import torch
+
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        except Exception:  # noqa: BLE001
+            pass
+        return {"error": f"{type(e).__name__}: {str(e)[:300]}"}
 
 
 def run_large(args, stream):

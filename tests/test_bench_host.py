@@ -57,3 +57,12 @@ def test_force_counters_follow_the_source(bench, tmp_path, monkeypatch):
     (tmp_path / "paper_1105_5613_gb300" / "csrc" / "k_force.cu").write_text(src + " ")
     assert bench.force_traffic(1000) is None
     assert bench.force_issue(1_000_000, 1.0, 4, 2000.0) is None
+
+
+def test_a_failing_secondary_leg_is_reported_not_fatal(bench):
+    def boom(x):
+        raise MemoryError(f"no room for {x} particles")
+
+    assert bench.optional_leg(lambda a, b: a + b, 2, 3) == 5
+    r = bench.optional_leg(boom, 1024191500)
+    assert r == {"error": "MemoryError: no room for 1024191500 particles"}

@@ -66,3 +66,29 @@ def test_a_failing_secondary_leg_is_reported_not_fatal(bench):
     assert bench.optional_leg(lambda a, b: a + b, 2, 3) == 5
     r = bench.optional_leg(boom, 1024191500)
     assert r == {"error": "MemoryError: no room for 1024191500 particles"}
+
+
+def test_bench_runs_end_to_end_against_standins():
+    """Every leg of bench.py through its host code, with the library and CUDA replaced by
+    stand-ins (tests/bench_standins.py); the one JSON line carries every key of the
+    contract and no leg reports an error."""
+    import subprocess
+    import sys
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, os.path.join(here, "bench_standins.py")],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
+              "roofline", "cpu_baseline", "gpu_launches"):
+        assert k in d, k
+    assert d["gpu_launches"] == 3 * 16 + 2
+    for leg in ("fp64", "soft_sphere", "replicas", "large", "cpu_baseline"):
+        assert "error" not in d[leg], d[leg]
+    assert {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"} <= set(d["e2e"])
+    assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(d["roofline"])
+    assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])

@@ -382,6 +382,49 @@ def test_steepest_descent_lowers_energy():
     assert E1 < E0
 
 
+def test_steepest_descent_step_rule():
+    """One step moves every particle by h F_i with h = min(hmax, dmax / max_i |F_i|): the
+    displacement is parallel to the force, and the largest one is dmax when the force cap
+    binds, hmax max|F| when it does not."""
+    n = 400
+    L = gen.box_for(n, 1.2)
+    pos = gen.rsa_positions(n, L, 0.7, 17)
+    sp = gen.assign_species(n, n // 5, 17)
+    p = oracle.ka_params()
+    F = oracle.forces(pos, sp, L, p)[0]
+    fmax = np.linalg.norm(F, axis=1).max()
+    # displacements stay below L/2 so that the minimum image recovers them
+    for hmax, dmax in ((1e-3, 0.05), (0.2 / fmax, 1.0)):
+        moved = oracle.sd_run(pos, sp, L, p, 1, hmax=hmax, dmax=dmax)
+        d = moved - pos
+        d -= L * np.round(d / L)
+        h = min(hmax, dmax / fmax)
+        assert np.allclose(d, h * F, rtol=1e-9, atol=1e-12)
+        assert np.linalg.norm(d, axis=1).max() == pytest.approx(min(dmax, hmax * fmax), rel=1e-9)
+
+
+def test_kinetic_energy_and_kick_use_each_species_mass():
+    """Species masses 1 and 3: K = sum m v^2 / 2 and P = sum m v by species, and one NVE
+    step of a resting pair of unlike particles changes each velocity by F dt / m (to
+    first order), so the heavier one moves a third as fast."""
+    p = oracle.ka_params(mass=(1.0, 3.0))
+    rng = np.random.default_rng(4)
+    vel = rng.normal(size=(10, 3))
+    sp = np.array([0, 1] * 5, dtype=np.uint8)
+    K, P = oracle.kinetic(vel, sp, p)
+    m = np.where(sp == 1, 3.0, 1.0)
+    assert K == pytest.approx(0.5 * (m[:, None] * vel ** 2).sum(), rel=1e-14)
+    assert np.allclose(P, (m[:, None] * vel).sum(0), rtol=1e-14, atol=1e-14)
+    L, r0, dt = 9.0, 1.0, 1e-4
+    pos = np.array([[2.0, 3.0, 4.0], [2.0 + r0, 3.0, 4.0]])
+    st = oracle.MDState(pos, np.zeros((2, 3)), np.array([0, 1], dtype=np.uint8), L, p)
+    oracle.md_run(st, 1, dt)
+    f = oracle.forces(pos, np.array([0, 1], dtype=np.uint8), L, p)[0]
+    assert np.allclose(st.vel[0], f[0] * dt / 1.0, rtol=1e-3)
+    assert np.allclose(st.vel[1], f[1] * dt / 3.0, rtol=1e-3)
+    assert st.vel[1, 0] == pytest.approx(-st.vel[0, 0] / 3.0, rel=1e-3)
+
+
 # ------------------------------------------------------------------- observables ----
 
 def test_gr_counts_against_pdist():

@@ -31,6 +31,7 @@ struct bbmd_sim {
     int gr_nbins = 0;
     bool ref_set = false;
     int sticky = 0;
+    int device = 0;                  // CUDA device of the handle (current at creation)
     int nsm = 1;
     int graph_gen = 0;               // bumped whenever captured launch arguments go stale
     long long tune_step = 0, tune_rebuilds = 0;  // counters at the last shape tuning
@@ -72,6 +73,27 @@ void dev_free(bbmd_sim* s, void* p) {
     else
         cudaFree(p);
 }
+
+// Makes `dev` the calling thread's current device for the lifetime of the guard and puts
+// the caller's device back afterwards, so that every call on a handle works on the device
+// the handle was created on whatever device the caller has current.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+            return;
+        }
+        if (prev == dev) prev = -1;
+        else cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
 
 bbmd_status fail(bbmd_sim* s, bbmd_status code, const std::string& msg) {
     if (s) s->err = msg;
@@ -456,6 +478,11 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     }
     bbmd_sim* sim = new bbmd_sim();
     sim->P = *params;
+    if (cudaGetDevice(&sim->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete sim;
+        return BBMD_ERR_CUDA;
+    }
     sim->st = (cudaStream_t)stream;
     if (!sim->st) {
         if (cudaStreamCreateWithFlags(&sim->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -513,9 +540,8 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
         return BBMD_ERR_CUDA;
     }
     // device properties and grids
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, sim->device);
     if (nsm <= 0) nsm = 1;
     // per-particle grid-stride kernels: 8 CTAs per SM, fewer for a small system
     D.grid_part = (int32_t)std::min<int64_t>((int64_t)nsm * 8, std::max<int64_t>(1, (n + 255) / 256));
@@ -636,6 +662,7 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
 
 void bbmd_destroy(bbmd_sim* sim) {
     if (!sim) return;
+    DeviceGuard dg(sim->device);
     if (sim->st) cudaStreamSynchronize(sim->st);
     else cudaDeviceSynchronize();
     free_graphs(sim);
@@ -647,6 +674,7 @@ void bbmd_destroy(bbmd_sim* sim) {
 bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* th,
                                double* ms, int64_t* rebuilds) {
     if (!sim) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     if (nsteps < 0 || nsteps > 0x7fffffff || !(dt > 0.0) || !(dt < 1.0))
         return fail(sim, BBMD_ERR_ARG, "nsteps in [0, 2^31) and dt in (0, 1) required");
     int nh = th && th->kind == BBMD_THERMO_NH;
@@ -693,6 +721,7 @@ bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt, const b
 
 bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* th) {
     if (!sim) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     if (nsteps < 0 || nsteps > 0x7fffffff || !(dt > 0.0) || !(dt < 1.0))
         return fail(sim, BBMD_ERR_ARG, "nsteps in [0, 2^31) and dt in (0, 1) required");
     int nh = 0;
@@ -720,6 +749,7 @@ bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_therm
 
 bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args, bbmd_obs* out) {
     if (!sim || !out) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     int nbins = args && args->nbins > 0 ? args->nbins : 500;
     double rmax = args && args->rmax > 0.0 ? args->rmax : 5.0;
     double kv = args && args->k > 0.0 ? args->k : 7.25;
@@ -836,6 +866,7 @@ bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args
 
 bbmd_status bbmd_minimize(bbmd_sim* sim, int64_t nsteps, double hmax, double dmax) {
     if (!sim || nsteps < 0 || !(hmax > 0.0) || !(dmax > 0.0)) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     for (int64_t k = 0; k < nsteps; ++k) {
         launch_force(sim->d, sim->st, false, false);
         launch_sd_step(sim->d, sim->st, hmax, dmax);
@@ -850,6 +881,7 @@ bbmd_status bbmd_minimize(bbmd_sim* sim, int64_t nsteps, double hmax, double dma
 
 bbmd_status bbmd_get_state(bbmd_sim* sim, double* pos, double* vel, int32_t* image) {
     if (!sim) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     const int64_t n = sim->d.n;
     double* tp = pos ? (double*)dev_alloc(sim, 3 * n * 8) : nullptr;
     double* tv = vel ? (double*)dev_alloc(sim, 3 * n * 8) : nullptr;
@@ -877,6 +909,7 @@ bbmd_status bbmd_get_state(bbmd_sim* sim, double* pos, double* vel, int32_t* ima
 bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
                            const int32_t* image) {
     if (!sim || !pos || !vel) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     const int64_t n = sim->d.n;
     double* tp = (double*)dev_alloc(sim, 3 * n * 8);
     double* tv = (double*)dev_alloc(sim, 3 * n * 8);
@@ -920,6 +953,7 @@ bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
 bbmd_status bbmd_get_forces_ids(bbmd_sim* sim, const int64_t* ids, int64_t m, double* F,
                                 double* u) {
     if (!sim || !ids || !F || m < 0) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     const int64_t n = sim->d.n;
     for (int64_t t = 0; t < m; ++t)
         if (ids[t] < 0 || ids[t] >= n) return fail(sim, BBMD_ERR_ARG, "ids must be in [0, n)");
@@ -953,6 +987,7 @@ bbmd_status bbmd_get_forces_ids(bbmd_sim* sim, const int64_t* ids, int64_t m, do
 
 bbmd_status bbmd_get_forces(bbmd_sim* sim, double* F, double* u) {
     if (!sim || !F) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     const int64_t n = sim->d.n;
     launch_force(sim->d, sim->st, u != nullptr, false);
     double* tf = (double*)dev_alloc(sim, 3 * n * 8);
@@ -976,6 +1011,7 @@ bbmd_status bbmd_get_forces(bbmd_sim* sim, double* F, double* u) {
 
 bbmd_status bbmd_get_cells(bbmd_sim* sim, int64_t* cell) {
     if (!sim || !cell) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     const int64_t n = sim->d.n;
     int64_t* tc = (int64_t*)dev_alloc(sim, n * 8);
     if (!tc) return fail(sim, BBMD_ERR_OOM, "get_cells");
@@ -991,6 +1027,7 @@ bbmd_status bbmd_get_cells(bbmd_sim* sim, int64_t* cell) {
 bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int64_t* offsets,
                                int64_t* nbr, int64_t cap) {
     if (!sim || !offsets) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     if (sim->d.nbr_mode != BBMD_NBR_VERLET) return fail(sim, BBMD_ERR_STATE, "no stored list in cell mode");
     {
         const bbmd_status g = read_status(sim);  // grows cut lists first
@@ -1061,6 +1098,7 @@ bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int
 
 bbmd_status bbmd_tune(bbmd_sim* sim) {
     if (!sim) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     if (sim->shapes.size() < 2) return BBMD_OK;
     // weight of the list build: the rebuilds per step seen since the last tuning (a rebuild
     // about every four steps when fewer than 20 steps were taken)
@@ -1082,6 +1120,7 @@ bbmd_status bbmd_tune(bbmd_sim* sim) {
 
 bbmd_status bbmd_rebuild(bbmd_sim* sim) {
     if (!sim) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     bbmd_status rc = rebuild_now(sim);
     if (rc != BBMD_OK) return rc;
     launch_force(sim->d, sim->st, false, false);
@@ -1126,6 +1165,7 @@ struct bbmd_batch {
     std::vector<cudaStream_t> side;  // capture streams of the branches
     std::vector<cudaEvent_t> ev;     // fork + joins
     std::string err;
+    int device = 0;                  // CUDA device of every replica (current at creation)
 };
 
 namespace {
@@ -1323,6 +1363,7 @@ extern "C" {
 
 void bbmd_destroy_batch(bbmd_batch* b) {
     if (!b) return;
+    DeviceGuard dg(b->device);
     if (b->st) cudaStreamSynchronize(b->st);
     batch_free_graphs(b);
     batch_free_tables(b);
@@ -1343,6 +1384,11 @@ bbmd_status bbmd_create_batch(const bbmd_params* params, int32_t n_rep, const in
     if (!params || n_rep < 1 || n_rep > 65536 || !n || !box || !species || !T0)
         return BBMD_ERR_ARG;
     bbmd_batch* b = new bbmd_batch();
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return BBMD_ERR_CUDA;
+    }
     b->st = (cudaStream_t)stream;
     if (!b->st) {
         if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1368,6 +1414,7 @@ bbmd_status bbmd_create_batch(const bbmd_params* params, int32_t n_rep, const in
 
 bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd_thermostat* th) {
     if (!b) return BBMD_ERR_ARG;
+    DeviceGuard dg(b->device);
     if (nsteps < 0 || nsteps > 0x7fffffff || !(dt > 0.0) || !(dt < 1.0))
         return batch_fail(b, BBMD_ERR_ARG, "nsteps in [0, 2^31) and dt in (0, 1) required");
     int nh = 0;
@@ -1459,6 +1506,7 @@ bbmd_status noalloc_setup(bbmd_sim* sim, int dev) {
 extern "C" bbmd_status bbmd_gr_counts_noalloc(bbmd_sim* sim, int32_t nbins, double rmax,
                                               uint64_t* counts) {
     if (!sim || !counts) return BBMD_ERR_ARG;
+    DeviceGuard dg(sim->device);
     if (nbins <= 0) nbins = 500;
     if (!(rmax > 0.0)) rmax = 5.0;
     if (nbins > kNoAllocBins) return fail(sim, BBMD_ERR_ARG, "nbins <= 4096");
@@ -1478,8 +1526,7 @@ extern "C" bbmd_status bbmd_gr_counts_noalloc(bbmd_sim* sim, int32_t nbins, doub
                     "g(r) without allocation: the coarse-grid search needs " +
                         std::to_string(need) + " int32 scratch entries, the fixed array holds " +
                         std::to_string(kNoAllocInts) + " (use bbmd_observe)");
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
+    const int dev = sim->device;
     if (dev < 0 || dev >= kNoAllocDevices) return fail(sim, BBMD_ERR_ARG, "device ordinal >= 64");
     bbmd_status rc = noalloc_setup(sim, dev);
     if (rc != BBMD_OK) return rc;

@@ -261,7 +261,6 @@ def test_neighbor_sets_brute_cells_and_kdtree():
     for (i, j), s, ins in zip(pairs, sure, inside):
         if s:
             assert (j in sets[i]) == bool(ins)
-    assert sum(len(s) for s in sets) == 2 * int((inside | ~sure).sum()) - 2 * int((~sure & ~inside).sum()) or True
     expect_total = 2 * int((inside & sure).sum())
     got_total = sum(len(s) for s in sets)
     assert abs(got_total - expect_total) <= 2 * int((~sure).sum())
@@ -341,6 +340,77 @@ def test_nose_hoover_free_gas_matches_ode():
                           t_eval=[t_end])
     assert lg[-1, 0] == pytest.approx(sol.y[0, -1], rel=2e-4)
     assert st.nh.xi == pytest.approx(sol.y[1, -1], rel=2e-3, abs=2e-4)
+
+
+def test_nose_hoover_ramp_follows_the_ode_with_stepwise_targets():
+    """Linear cooling (Sec. 4): step k of a call of nsteps steps thermostats to
+    T_k = T_start + (T_end - T_start) k / nsteps, constant within the step, with Q = g T_k
+    tau^2.  On a free gas the Nose-Hoover equations reduce to dK/dt = -2 xi K and
+    dxi/dt = (2K - g T_k) / (g T_k tau^2); scipy integrates them step interval by step
+    interval and the oracle must land on the same K and xi.  A target taken one step late
+    or early (k + 1, or nsteps - 1 in the ratio) moves K by about 1e-2 here, against an
+    integrator error near 1e-5."""
+    integ = pytest.importorskip("scipy.integrate")
+    n = 400
+    L = gen.box_for(n, 0.01)
+    rng = np.random.default_rng(21)
+    pos = rng.uniform(0, L, (n, 3))
+    sp = np.zeros(n, dtype=np.uint8)
+    vel = gen.maxwell_boltzmann(n, 2.0, 21, np.ones(n))
+    p = oracle.ka_params()
+    for a in range(2):
+        for b in range(2):
+            p.eps[a][b] = 0.0  # non-interacting
+    T0, T1, tau, dt, nsteps = 2.0, 0.3, 0.2, 0.002, 100
+    st = oracle.MDState(pos, vel, sp, L, p)
+    lg = oracle.md_run(st, nsteps, dt, thermo=(T0, T1, tau), log=True)
+    g = 3 * n - 3
+    # the recorded target of the first and of the last step of the call
+    assert lg[0, 4] == T0
+    assert lg[-1, 4] == pytest.approx(T0 + (T1 - T0) * (nsteps - 1) / nsteps, rel=1e-15)
+    y = [oracle.kinetic(vel, sp, p)[0], 0.0]
+    Ks = []
+    for k in range(nsteps):
+        Tk = T0 + (T1 - T0) * k / nsteps
+        Q = g * Tk * tau * tau
+
+        def rhs(t, yy, Tk=Tk, Q=Q):
+            return [-2.0 * yy[1] * yy[0], (2.0 * yy[0] - g * Tk) / Q]
+
+        sol = integ.solve_ivp(rhs, (0.0, dt), y, rtol=1e-12, atol=1e-12, method="DOP853")
+        y = [sol.y[0, -1], sol.y[1, -1]]
+        Ks.append(y[0])
+    assert np.allclose(lg[:, 0], Ks, rtol=1e-4)
+    assert st.nh.xi == pytest.approx(y[1], rel=1e-4, abs=1e-5)
+    # and the thermostat followed the ramp down: K well below its start
+    assert lg[-1, 0] < 0.7 * lg[0, 0]
+
+
+def test_wrap_image_counters_of_free_particles():
+    """Free particles at constant velocity cross the periodic box several times in both
+    directions: the stored position plus L times the image counter is the straight line
+    x0 + v t, and the counter is floor((x0 + v t) / L) (the number of boxes crossed)."""
+    n = 24
+    L = 9.0
+    rng = np.random.default_rng(31)
+    x0 = rng.uniform(0, L, (n, 3))
+    v = rng.uniform(-12.0, 12.0, (n, 3))
+    v[0] = [11.5, -11.5, 0.0]
+    sp = np.zeros(n, dtype=np.uint8)
+    p = oracle.ka_params()
+    for a in range(2):
+        for b in range(2):
+            p.eps[a][b] = 0.0  # no forces: straight lines
+    dt, nsteps = 0.01, 500
+    st = oracle.MDState(x0, v, sp, L, p)
+    oracle.md_run(st, nsteps, dt)
+    line = x0 + v * (nsteps * dt)
+    assert np.abs(st.pos + L * st.image - line).max() < 1e-10
+    expect = np.floor(line / L)
+    clear = np.abs(line / L - np.round(line / L)) > 1e-9  # not on a box face
+    assert np.array_equal(st.image[clear], expect[clear].astype(np.int32))
+    assert st.image.min() <= -5 and st.image.max() >= 5  # several boxes, both directions
+    assert np.all((st.pos >= 0.0) & (st.pos < L))
 
 
 def test_nose_hoover_extended_energy_conserved():

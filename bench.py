@@ -37,7 +37,7 @@ T_HIGH, T_LOW, TAU, DT = 2.0, 0.4, 0.5, 0.005
 NCELL_FCC = 160                      # N = 4 * 160^3 = 16,384,000
 FLOP_PER_HALF_PAIR = 25.0            # r^2, reciprocal, LJ force scalar and vector update
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SM_COUNT, FP32_PER_SM_CLK = 152, 128
+FP32_PER_SM_CLK = 128                # FP32 lanes per SM (nominal, for the derived peak)
 
 
 def _dist():
@@ -262,6 +262,9 @@ def run_ours(args):
     block_z = sim.info()["block_z"]
     clocks = clk.summary()
 
+    # ---- measured FP32 / FP64 FMA peaks of this GPU (the ALU roofline denominators) ----
+    probe = optional_leg(fma_probe, bbmd, local_gpu)
+
     # ---- per-phase attribution (same steps, phases launched one by one) ----
     nprof = max(2, min(args.steps, 10))
     phases, nreb = sim.step_profiled(nprof, DT, therm(nprof))
@@ -347,14 +350,18 @@ def run_ours(args):
 
     soft = optional_leg(leg_soft) if args.soft_steps > 0 else None
     replicas = optional_leg(run_replicas, args, stream) if args.replicas > 0 else None
-    large = (optional_leg(run_large, args, stream)
+    peak_for_large = probe.get("fp32_tflops") if isinstance(probe, dict) else None
+    large = (optional_leg(run_large, args, stream, peak_for_large)
              if args.large_steps > 0 or args.large_fp64_steps > 0 else None)
     if rank != 0:
         return None
     value = whole_job_rate(n * args.steps, ws, ms)
     pk = peaks()
     clock_mhz = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_PER_SM_CLK * 2 * clock_mhz * 1e6 / 1e12  # TFLOP/s
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    derived = nsm * FP32_PER_SM_CLK * 2 * clock_mhz * 1e6 / 1e12  # TFLOP/s
+    measured = probe.get("fp32_tflops") if isinstance(probe, dict) else None
+    fp32_peak = measured or derived
     hp_per = half_pairs_per_particle()
     flops_launch = n * hp_per * FLOP_PER_HALF_PAIR
     achieved = flops_launch / (force_ms / 1e3) / 1e12
@@ -380,10 +387,16 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_force (Verlet list, NH kinetic partials)",
                      "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
+                     "peak_source": ("measured: FP32 FMA-chain probe (bbmd_fma_peak), this run"
+                                     if measured else
+                                     f"derived: {nsm} SMs x {FP32_PER_SM_CLK} FP32 lanes x 2 "
+                                     f"flop x {clock_mhz:.0f} MHz"),
+                     "peak_derived": derived,
                      "algorithmic": f"{hp_per:.2f} half pairs/particle x {FLOP_PER_HALF_PAIR:.0f} "
                                     f"flop x {n} particles per launch",
                      "force_ms": force_ms,
-                     "issue": force_issue(n, force_ms, block_z, clock_mhz)},
+                     "issue": force_issue(n, force_ms, block_z, clock_mhz, nsm)},
+        "fma_probe": probe,
         "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
         "block_z": block_z,
         "rebuilds_per_step": nreb / nprof,
@@ -419,11 +432,14 @@ def optional_leg(fn, *a):
         return {"error": f"{type(e).__name__}: {str(e)[:300]}"}
 
 
-def run_large(args, stream):
-    """The 1,024,191,500-particle step: FCC 4*635^3 (80:20) at rho = 1.2, T = 0.6 NVE,
-    dt = 0.005, forces from the cell stencil on the fly (no stored Verlet list), positions
-    and velocities generated on the device; mixed precision timed over args.large_steps
-    steps, then the FP64 form over args.large_fp64_steps steps (one handle at a time)."""
+def run_large(args, stream, fp32_peak=None):
+    """The 1,024,191,500-particle step: FCC 4*635^3 (80:20) at rho = 1.2, displaced by the
+    generator's seeded jitter (0.05 per coordinate), T = 0.6 NVE, dt = 0.005, forces from
+    the cell stencil on the fly (no stored Verlet list), positions and velocities
+    generated on the device.  Mixed precision: args.large_untimed untimed steps, then
+    args.large_steps timed steps, then 2 steps phase by phase (per-phase split and the
+    roofline of the cell-mode force kernel); then the FP64 form over
+    args.large_fp64_steps steps (one handle at a time)."""
     import torch
 
     from inputs import generate as gen
@@ -436,19 +452,21 @@ def run_large(args, stream):
     t0 = time.perf_counter()
     sp = gen.assign_species(n, n // 5, 0)
     t_species = time.perf_counter() - t0
-    out = {"workload": f"large step, N={n} (4*{ncell}^3 FCC, 80:20), rho=1.2, T=0.6 NVE, "
-                       "dt=0.005, cell stencil on the fly (no stored list)",
+    out = {"workload": f"large step, N={n} (4*{ncell}^3 FCC jittered by 0.05, 80:20), "
+                       "rho=1.2, T=0.6 NVE, dt=0.005, cell stencil on the fly (no stored list)",
            "n_particles": n, "box": L, "species_host_s": t_species}
     for prec, steps, key in ((bbmd.PREC_MIXED, args.large_steps, "mixed"),
                              (bbmd.PREC_FP64, args.large_fp64_steps, "fp64")):
         if steps <= 0:
             continue
-        p = bbmd.ka_params(precision=prec, nbr_mode=bbmd.NBR_CELL)
+        p = bbmd.ka_params(precision=prec, nbr_mode=bbmd.NBR_CELL, init_jitter=0.05)
         t0 = time.perf_counter()
         sim = bbmd.Sim(p, n, L, sp, None, None, T0=0.6, seed=0, stream=stream.cuda_stream)
         t_create = time.perf_counter() - t0
-        sim.step(1, DT)
+        untimed = args.large_untimed if prec == bbmd.PREC_MIXED else 1
+        sim.step(untimed, DT)
         stream.synchronize()
+        r0 = sim.observe(0)["n_rebuilds"]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         sim.step(steps, DT)
@@ -456,11 +474,27 @@ def run_large(args, stream):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         info = sim.info()
-        obs = sim.observe(bbmd.OBS_ENERGY)
+        obs = sim.observe(0)  # kinetic only: the FP64 energy pass of 1e9 particles takes ~20 s
         out[key] = {"value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps,
+                    "untimed_steps_before": untimed,
                     "ms_per_step": ms / steps, "create_s": t_create, "block_z": info["block_z"],
-                    "device_gb": info["device_bytes"] / 1e9, "T": obs["temperature"],
-                    "pe_per_particle": obs["pe"] / n}
+                    "rebuilds_per_step": (obs["n_rebuilds"] - r0) / steps,
+                    "device_gb": info["device_bytes"] / 1e9, "T": obs["temperature"]}
+        if prec == bbmd.PREC_MIXED:
+            nprof = 2
+            ph, nreb = sim.step_profiled(nprof, DT)
+            force_ms = ph["force"] / nprof
+            out[key]["phases_ms_per_step"] = {k: v / nprof for k, v in ph.items()}
+            out[key]["phase_rebuilds"] = nreb
+            if fp32_peak:
+                hp_per = half_pairs_per_particle()
+                ach = n * hp_per * FLOP_PER_HALF_PAIR / (force_ms / 1e3) / 1e12
+                out[key]["roofline"] = {
+                    "bound": "alu", "kernel": "k_force (cell stencil on the fly, NVE)",
+                    "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "force_ms": force_ms,
+                    "algorithmic": f"{hp_per:.2f} half pairs/particle x "
+                                   f"{FLOP_PER_HALF_PAIR:.0f} flop x {n} particles per launch"}
         sim.close()
         del sim
     return out
@@ -509,6 +543,18 @@ def run_replicas(args, stream):
             "T_first_last": Ts}
 
 
+def fma_probe(bbmd, gpu=None):
+    """Measured FP32 and FP64 fused multiply-add peaks of this GPU (bbmd_fma_peak: FMA
+    chains with no memory traffic, CUDA events, best of 3), with the SM clocks sampled
+    while it ran."""
+    clk = ClockSampler(gpu=gpu)
+    with clk:
+        f32, nsm = bbmd.fma_peak(bbmd.PREC_MIXED)
+        f64, _ = bbmd.fma_peak(bbmd.PREC_FP64)
+    return {"fp32_tflops": f32, "fp64_tflops": f64, "sm_count": nsm,
+            "clocks": clk.summary()}
+
+
 def ctypes_sizeof_obs(bbmd):
     import ctypes
 
@@ -538,13 +584,13 @@ def force_traffic(n):
     return rec["bytes_per_particle"] * n if rec else None
 
 
-def force_issue(n, force_ms, block_z, clock_mhz):
+def force_issue(n, force_ms, block_z, clock_mhz, nsm):
     """Issue-slot view of the same launch: warp instructions (from the ncu record, same
     block shape) per second against 4 warp instructions per SM per cycle."""
     rec = force_counters()
     if not rec or rec.get("block_z") != block_z or "warp_inst_per_particle" not in rec:
         return None
-    peak = SM_COUNT * 4 * clock_mhz * 1e6
+    peak = nsm * 4 * clock_mhz * 1e6
     rate = rec["warp_inst_per_particle"] * n / (force_ms / 1e3)
     return {"warp_inst_per_s": rate, "peak": peak, "frac": rate / peak,
             "warp_inst_per_particle": rec["warp_inst_per_particle"]}
@@ -612,11 +658,19 @@ def run_reference(args):
     v = n * args.steps / dt
     sample = (f"N={n} (4*20^3 FCC, same mixture, rho=1.2, NH ramp) per step, FP64 oracle, "
               f"single thread")
+    # the config names what this arm timed: a bounded sample of the workload
+    config = workload_config(args, ws)
+    config["sample_of"] = config["workload"]
+    config["workload"] = (f"bounded sample of the supercooling quench: N={n} (4*20^3 FCC, "
+                          "80:20), rho=1.2, same Nose-Hoover ramp and dt, FP64 oracle, "
+                          "single thread")
+    config["n_particles"] = n
+    config["box"] = L
     return {"impl": "reference", "metric": "particle-steps/s (binary LJ, 16M & 1.02B N) mixed vs "
             "FP64 GPU; % of roofline", "value": v, "unit": "particle-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args, ws),
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
@@ -643,8 +697,10 @@ def main():
     ap.add_argument("--replicas", type=int, default=64,
                     help="number of replicas of the batched-replica leg (0 = skip)")
     ap.add_argument("--replica-steps", type=int, default=500)
-    ap.add_argument("--large-steps", type=int, default=3,
+    ap.add_argument("--large-steps", type=int, default=20,
                     help="timed mixed-precision steps of the 1.02e9-particle cell-mode step")
+    ap.add_argument("--large-untimed", type=int, default=5,
+                    help="untimed steps of the large step before its timed steps")
     ap.add_argument("--large-fp64-steps", type=int, default=1,
                     help="timed steps of the FP64 form of the large step")
     ap.add_argument("--large-ncell", type=int, default=635,

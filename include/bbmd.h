@@ -88,7 +88,11 @@ enum { BBMD_THERMO_NVE = 0, BBMD_THERMO_NH = 1 };
  *   4 x 4 x (block_z + 2) cells around it (0 = from the density, with 15 % headroom).
  * block_z: block shape of the force and list kernels, 2 x 2 x block_z cells per CTA:
  *   0 = chosen at creation by timing every shape that fits (1, 2, 4, 8) on the initial
- *   state; 1, 2, 4 or 8 = that shape. */
+ *   state; 1, 2, 4 or 8 = that shape.
+ * init_jitter: with pos == NULL (device-generated FCC lattice), coordinate d of site i is
+ *   moved by init_jitter * (2u - 1), u = uniform01(draw 3i + d of stream 5) under the
+ *   creation seed (0 = the perfect lattice); the displaced position is quantised and
+ *   reduced into the box like any input position. */
 typedef struct {
     int32_t potential;
     int32_t shift;
@@ -102,6 +106,7 @@ typedef struct {
     int32_t list_capacity;
     int32_t stencil_capacity;
     int32_t block_z;
+    double init_jitter;
 } bbmd_params;
 
 /* Thermostat of one bbmd_step call.  NVE, or Nose-Hoover with one friction variable xi,
@@ -346,6 +351,16 @@ bbmd_status bbmd_gr_counts_noalloc(bbmd_sim* sim, int32_t nbins, double rmax, ui
 
 /* Message of the last failed call on this handle ("" if none). */
 const char* bbmd_last_error(const bbmd_sim* sim);
+
+/* Measured peak fused multiply-add rate of the current device, in TFLOP/s (2 flops per
+ * FMA): precision BBMD_PREC_MIXED -> FP32, BBMD_PREC_FP64 -> FP64.  *sm_count (may be
+ * NULL) receives the device's multiprocessor count.  A measurement helper: the roofline
+ * denominator of the pair-force kernels, which are bound by arithmetic issue, not by
+ * memory; the paper has no counterpart.  Every thread of 8 CTAs of 256 threads per SM
+ * runs 8 independent FMA chains with no memory traffic; the best of 3 timed launches
+ * (CUDA events) after a warm-up launch is reported.  Allocates a few KB of device memory
+ * for the duration of the call; synchronising; about half a second. */
+bbmd_status bbmd_fma_peak(int32_t precision, int32_t* sm_count, double* tflops);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,7 @@ STREAM_SPECIES = 1
 STREAM_VEL = 2
 STREAM_RSA = 3
 STREAM_REPLICA = 4
+STREAM_JITTER = 5
 
 _TWO_M53 = 2.0 ** -53
 
@@ -93,16 +94,25 @@ def fcc_lattice(ncell: int, L: float) -> np.ndarray:
     return pos.reshape(-1, 3)
 
 
-def fcc_sites(ncell: int, L: float, idx: np.ndarray) -> np.ndarray:
+def fcc_sites(ncell: int, L: float, idx: np.ndarray, jitter: float = 0.0,
+              seed: int = 0) -> np.ndarray:
     """Positions of the FCC sites ``idx`` (same numbering and values as
-    :func:`fcc_lattice`), without building the whole lattice."""
+    :func:`fcc_lattice`), without building the whole lattice.  With ``jitter > 0``
+    coordinate ``d`` of site ``i`` is moved by ``jitter * (2 u - 1)``, ``u`` the uniform
+    draw ``3 i + d`` of the jitter stream (evaluated as written, no fused multiply-add;
+    the result may leave the box and is reduced into it by the quantisation)."""
     n = int(ncell)
     a = L / n
     idx = np.asarray(idx, dtype=np.int64)
     b = idx % 4
     c = idx // 4
     cells = np.stack([c % n, (c // n) % n, c // (n * n)], axis=1).astype(np.float64)
-    return (cells + _FCC_BASIS[b] + 0.25) * a
+    pos = (cells + _FCC_BASIS[b] + 0.25) * a
+    if jitter > 0.0:
+        ctr = (3 * idx[:, None] + np.arange(3)[None, :]).astype(np.uint64)
+        u = uniform01(counter_u64(seed, STREAM_JITTER, ctr))
+        pos = pos + float(jitter) * (2.0 * u - 1.0)
+    return pos
 
 
 def assign_species(n: int, n_b: int, seed: int) -> np.ndarray:

@@ -41,6 +41,7 @@ class bbmd_params(C.Structure):
         ("eps", (C.c_double * 2) * 2), ("sigma", (C.c_double * 2) * 2),
         ("rcut", (C.c_double * 2) * 2), ("mass", C.c_double * 2), ("skin", C.c_double),
         ("list_capacity", C.c_int32), ("stencil_capacity", C.c_int32), ("block_z", C.c_int32),
+        ("init_jitter", C.c_double),
     ]
 
 
@@ -88,7 +89,7 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_get_forces_ids", "bbmd_create_batch", "bbmd_step_batch",
            "bbmd_batch_replica", "bbmd_batch_size", "bbmd_batch_set_branches",
            "bbmd_destroy_batch",
-           "bbmd_batch_last_error"]
+           "bbmd_batch_last_error", "bbmd_fma_peak"]
 
 _lib = None
 
@@ -157,6 +158,8 @@ def load(path: str | None = None):
     L.bbmd_batch_last_error.restype = C.c_char_p
     L.bbmd_last_error.argtypes = [vp]
     L.bbmd_last_error.restype = C.c_char_p
+    L.bbmd_fma_peak.argtypes = [C.c_int32, P(C.c_int32), P(d)]
+    L.bbmd_fma_peak.restype = C.c_int
     _lib = L
     return L
 
@@ -173,7 +176,7 @@ def _check(h, rc):
 
 def ka_params(potential=POT_LJ, shift=SHIFT_ENERGY, precision=PREC_MIXED, nbr_mode=NBR_VERLET,
               skin=0.3, rc_factor=2.5, mass=(1.0, 1.0), list_capacity=0, stencil_capacity=0,
-              block_z=0):
+              block_z=0, init_jitter=0.0):
     """Parameters of the binary mixture of the paper's benchmark suite (Sec. 3):
     eps_AA=1, eps_AB=1.5, eps_BB=0.5, sigma_AA=1, sigma_AB=0.8, sigma_BB=0.88, m=1."""
     p = bbmd_params()
@@ -190,7 +193,17 @@ def ka_params(potential=POT_LJ, shift=SHIFT_ENERGY, precision=PREC_MIXED, nbr_mo
     p.list_capacity = list_capacity
     p.stencil_capacity = stencil_capacity
     p.block_z = block_z
+    p.init_jitter = init_jitter
     return p
+
+
+def fma_peak(precision=PREC_MIXED):
+    """Measured peak FMA rate of the current device: (TFLOP/s, SM count)."""
+    L = load()
+    nsm = C.c_int32(0)
+    tf = C.c_double(0.0)
+    _check(None, L.bbmd_fma_peak(precision, C.byref(nsm), C.byref(tf)))
+    return tf.value, nsm.value
 
 
 def torch_allocator(device=None):

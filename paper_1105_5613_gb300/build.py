@@ -13,7 +13,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbbmd.so")
 # (source, object, extra flags): k_force.cu is compiled once per block shape
 SOURCES = [("bbmd_api.cu", "bbmd_api.o", []), ("k_sort.cu", "k_sort.o", []),
-           ("k_integrate.cu", "k_integrate.o", []), ("k_observe.cu", "k_observe.o", [])] + \
+           ("k_integrate.cu", "k_integrate.o", []), ("k_observe.cu", "k_observe.o", []),
+           ("k_probe.cu", "k_probe.o", [])] + \
           [("k_force.cu", f"k_force_z{z}.o", [f"-DBBMD_BLOCK_Z={z}"]) for z in (1, 2, 4, 8)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

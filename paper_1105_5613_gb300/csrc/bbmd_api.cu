@@ -228,6 +228,7 @@ bbmd_status validate(const bbmd_params* P, int64_t n, const double* box, std::st
     if (P->stencil_capacity < 0 || P->stencil_capacity > 65000) return msg = "stencil_capacity", BBMD_ERR_ARG;
     if (P->block_z != 0 && P->block_z != 1 && P->block_z != 2 && P->block_z != 4 && P->block_z != 8)
         return msg = "block_z must be 0 (autotune), 1, 2, 4 or 8", BBMD_ERR_ARG;
+    if (!(P->init_jitter >= 0.0 && P->init_jitter < 1e6)) return msg = "init_jitter", BBMD_ERR_ARG;
     return BBMD_OK;
 }
 
@@ -247,11 +248,12 @@ int shape_smax(const bbmd_sim* sim, int bz) {
     return (smax + 31) / 32 * 32;
 }
 
-// The staged region and its sentinel record must fit in shared memory (FP64 form: 32-byte
-// records) and its offsets in uint16 (the sentinel is smax itself).
+// The staged region and its sentinel record must fit in shared memory as 32-byte records
+// (the FP64 form, and the FP64 energy pass of mixed precision) and its offsets in uint16
+// (the sentinel is smax itself).
 bool shape_fits(const bbmd_sim* sim, int bz) {
     const int smax = shape_smax(sim, bz);
-    const size_t bytes = (size_t)(smax + 1) * (sim->P.precision == BBMD_PREC_FP64 ? 32 : 16);
+    const size_t bytes = (size_t)(smax + 1) * 32;
     return smax <= 65000 && bytes <= 200 * 1024;
 }
 
@@ -526,6 +528,11 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     double half = 0.5 * params->skin;
     D.disp2 = (float)(half * half * (1.0 - 1e-4));
     D.disp_thr = (float)(params->skin * (1.0 - 1e-4));
+    {
+        // cells two apart along an axis are more than one cell side apart
+        double dmin = std::ldexp((double)std::min(D.D[0], std::min(D.D[1], D.D[2])), -D.kexp);
+        D.disp_far = (float)((dmin - rcmax) * (1.0 - 1e-4));
+    }
     int lcap = params->list_capacity > 0 ? params->list_capacity : 160;
     D.lcap8 = (lcap + 7) / 8;
     double V = box[0] * box[1] * box[2];
@@ -632,7 +639,7 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     }
     if (rc == BBMD_OK) {
         launch_pack_state(D, sim->st, tpos, tvel, nullptr, false);
-        if (!pos) launch_init_fcc(D, sim->st, m_fcc);
+        if (!pos) launch_init_fcc(D, sim->st, m_fcc, params->init_jitter, seed);
         if (!vel) {
             double* tmp = (double*)dev_alloc(sim, (3 * n + 16) * 8);
             if (!tmp) rc = BBMD_ERR_OOM;

@@ -88,6 +88,8 @@ struct alignas(16) DevSim {
     float disp2;             // steepest descent: rebuild threshold on |x - x_build|^2
     float disp_thr;          // rebuild when two particles of the same or neighbouring build
                              // cells moved beyond it together (skin, FP32, conservative)
+    float disp_far;          // rebuild when any two particles moved beyond it together
+                             // (D_min - rc_max: pairs whose build cells are two apart)
     float* disp;             // [npad] displacement since the last build (integrate)
     float2* mtop;            // [ncell] two largest displacements per build cell
     PairTab pt;
@@ -309,7 +311,7 @@ void launch_finalize(const DevSim& s, cudaStream_t st, bool ke);
 void launch_finish(const DevSim& s, cudaStream_t st);
 void launch_state_sums(const DevSim& s, cudaStream_t st);          // KE, P partials -> sc->K etc.
 void launch_reduce_partials(const DevSim& s, cudaStream_t st, int nq, double* out_dev);
-void launch_init_fcc(const DevSim& s, cudaStream_t st, int m);
+void launch_init_fcc(const DevSim& s, cudaStream_t st, int m, double jitter, uint64_t seed);
 void launch_init_mb(const DevSim& s, cudaStream_t st, double T0, uint64_t seed, double* tmp3);
 void launch_sd_step(const DevSim& s, cudaStream_t st, double hmax, double dmax);
 void launch_clear_rebuild(const DevSim& s, cudaStream_t st);

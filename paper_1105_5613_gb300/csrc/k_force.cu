@@ -395,48 +395,35 @@ __device__ __forceinline__ void load_tab(const DevSim& s, int si, LaneTab& T) {
 
 struct Acc {
     float fx, fy, fz;
-    double u, w;
 };
 
-// Force (and energy) of one pair; contributes only when `in`.  d = x_j - x_i.
-template <bool ENERGY, bool FSHIFT>
+// Force of one pair; contributes only when `in`.  d = x_j - x_i.  (Pair energies and the
+// virial are evaluated by the FP64 energy pass, from exact integer positions.)
+template <bool FSHIFT>
 __device__ __forceinline__ void pair_add(const LaneTab& T, bool b, float dx, float dy, float dz,
                                          float r2, bool in, Acc& a) {
-    // energy passes use the correctly rounded reciprocal and carry sigma^2 as hi + lo so
-    // that summed pair energies carry no rounding bias; force passes use the fast forms
-    float ir2 = ENERGY ? __frcp_rn(r2) : rcp_approx(r2);
-    float s2 = ENERGY ? fmaf(b ? T.sig21 : T.sig20, ir2, (b ? T.sgl1 : T.sgl0) * ir2)
-                      : (b ? T.sig21 : T.sig20) * ir2;
+    float ir2 = rcp_approx(r2);
+    float s2 = (b ? T.sig21 : T.sig20) * ir2;
     float s6 = s2 * s2 * s2;
     float f = (b ? T.e481 : T.e480) * ir2 * s6 * (s6 - T.cpot);
-    float ir = 0.f;
-    if (FSHIFT) {
-        ir = rsqrtf(r2);
-        f = fmaf(b ? T.fc1 : T.fc0, ir, f);
-    }
+    if (FSHIFT) f = fmaf(b ? T.fc1 : T.fc0, rsqrtf(r2), f);
     f = in ? f : 0.f;
     a.fx = fmaf(f, dx, a.fx);
     a.fy = fmaf(f, dy, a.fy);
     a.fz = fmaf(f, dz, a.fz);
-    if (ENERGY) {
-        float V = (b ? T.e41 : T.e40) * s6 * (s6 - T.cpe) - (b ? T.vsh1 : T.vsh0);
-        if (FSHIFT) V -= (r2 * ir - (b ? T.rc1 : T.rc0)) * (b ? T.fc1 : T.fc0);
-        a.u += in ? (double)V : 0.0;
-        a.w += in ? (double)(f * r2) : 0.0;
-    }
 }
 
 // Fast path of one list pair (i, staged t), classified by d = r^2 - (middle of the band
 // around rc^2 for the species of j): interacting iff d <= -hw; |d| < hw is the band,
 // left to the exact fix-up; the smallest |d| of a batch tells whether it has band pairs.
-template <bool ENERGY, bool FSHIFT>
+template <bool FSHIFT>
 __device__ __forceinline__ void pair_fast(const LaneTab& T, float4 me, float4 p, Acc& a, float& near) {
     float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const bool b = p.w != 0.f;
     const float d = r2 - (b ? T.rm1 : T.rm0);
     near = fminf(near, fabsf(d));
-    pair_add<ENERGY, FSHIFT>(T, b, dx, dy, dz, r2, d <= -T.hw, a);
+    pair_add<FSHIFT>(T, b, dx, dy, dz, r2, d <= -T.hw, a);
 }
 
 // A staged copy is usable only in the minimum image (the 4x4x4 region holds a cell twice
@@ -448,7 +435,7 @@ __device__ __forceinline__ bool min_image_copy(const DevSim& s, float dx, float 
 // Exact decision for a band pair; adds its force if the FP64 rule says it interacts.
 // Kept out of line: it runs for a few pairs per million and must not add register
 // pressure to the batch loop.
-template <bool ENERGY, bool FSHIFT>
+template <bool FSHIFT>
 __device__ __noinline__ void pair_band(const DevSim& s, const Region& R, const LaneTab& T, float4 me, float4 p,
                           int t, int64_t gi, bool valid, Acc& a) {
     float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
@@ -458,7 +445,7 @@ __device__ __noinline__ void pair_band(const DevSim& s, const Region& R, const L
     if (!min_image_copy(s, dx, dy, dz)) return;
     int64_t gj = staged_global(R, t);
     if (r2_exact(s, gi, gj) < s.pt.rc2[T.si * 2 + (b ? 1 : 0)])
-        pair_add<ENERGY, FSHIFT>(T, b, dx, dy, dz, r2, true, a);
+        pair_add<FSHIFT>(T, b, dx, dy, dz, r2, true, a);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -467,8 +454,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// Block reduction of per-warp doubles into partials[q * kMaxPartials + lb].
-__device__ void block_partials(const DevSim& s, int lb, const double* wv, int nq) {
+// Block reduction of per-warp doubles wv[0 .. nq) (lane 0 of each warp) into
+// partials[(q0 + q) * kMaxPartials + lb], in a fixed order.
+__device__ void block_partials(const DevSim& s, int lb, const double* wv, int q0, int nq) {
     __shared__ double red[kBW][4];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
@@ -477,7 +465,7 @@ __device__ void block_partials(const DevSim& s, int lb, const double* wv, int nq
     if (threadIdx.x < nq) {
         double t = 0.0;
         for (int k = 0; k < kBW; ++k) t += red[k][threadIdx.x];
-        s.partials[threadIdx.x * kMaxPartials + lb] = t;
+        s.partials[(q0 + threadIdx.x) * kMaxPartials + lb] = t;
     }
 }
 
@@ -590,7 +578,7 @@ __device__ __forceinline__ bool force_selected(const DevSim& s) {
 }
 
 // MODE 0: Verlet list.  MODE 1: every particle of the 27-cell stencil (no stored list).
-template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+template <int MODE, bool KE, bool FSHIFT>
 __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     if (!force_selected<MODE>(s)) return;  // CTA-uniform, before any barrier
     extern __shared__ float4 smem[];
@@ -603,7 +591,6 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     // per-lane kinetic energy in compensated FP32 (sum + carried rounding error), reduced in
     // FP64 at the end; no FP64 instruction runs per chunk
     float ke_sum = 0.f, ke_err = 0.f;
-    double acc_u = 0.0, acc_w = 0.0;
     float hdt0 = 0.f, hdt1 = 0.f;
     if (KE) {
         hdt0 = s.sc->hdt[0];
@@ -668,7 +655,7 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                 const int si = me.w != 0.f ? 1 : 0;
                 LaneTab T;
                 load_tab(s, si, T);
-                Acc a = {0.f, 0.f, 0.f, 0.0, 0.0};
+                Acc a = {0.f, 0.f, 0.f};
                 if (MODE == 0) {
                     for (int kb = 0; kb < nkb; ++kb) {
                         const uint4 e = e0;
@@ -680,20 +667,20 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                             e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
                         }
                         float near = far;
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.x)], a, near);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.x)], a, near);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.y)], a, near);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.y)], a, near);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.z)], a, near);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.z)], a, near);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[lo16(e.w)], a, near);
-                        pair_fast<ENERGY, FSHIFT>(T, me, sm[hi16(e.w)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[lo16(e.x)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[hi16(e.x)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[lo16(e.y)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[hi16(e.y)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[lo16(e.z)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[hi16(e.z)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[lo16(e.w)], a, near);
+                        pair_fast<FSHIFT>(T, me, sm[hi16(e.w)], a, near);
                         const bool band = near < T.hw;
                         if (__any_sync(FULL, band) && band) {
                             const unsigned ws[4] = {e.x, e.y, e.z, e.w};
                             for (int q = 0; q < 8; ++q) {
                                 int t = (q & 1) ? hi16(ws[q >> 1]) : lo16(ws[q >> 1]);
-                                pair_band<ENERGY, FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
+                                pair_band<FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
                             }
                         }
                     }
@@ -783,7 +770,7 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                                 const float4 p = sm[rw[u]];
                                 const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
                                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                pair_add<ENERGY, FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
+                                pair_add<FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
                             }
                         }
 #else
@@ -796,7 +783,7 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                                 const float4 p = sm[ring[(cq + u) & (kRing - 1)]];
                                 const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
                                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                pair_add<ENERGY, FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
+                                pair_add<FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
                             }
                         }
 #endif
@@ -807,8 +794,7 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                 float fx = -a.fx, fy = -a.fy, fz = -a.fz;
                 if (act) {
                     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) set_status(s, ST_NONFINITE);
-                    s.F[gi] = make_float4(fx, fy, fz, ENERGY ? (float)(0.5 * a.u) : 0.f);
-                    if (ENERGY) s.ud[gi] = 0.5 * a.u;
+                    s.F[gi] = make_float4(fx, fy, fz, 0.f);
                 }
                 if (KE && act) {
                     if (MODE == 1) {
@@ -828,21 +814,12 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                     ke_err = (t - ke_sum) - y;
                     ke_sum = t;
                 }
-                if (ENERGY) {
-                    double uu = warp_sum_d(act ? 0.5 * a.u : 0.0);
-                    double ww = warp_sum_d(act ? 0.5 * a.w : 0.0);
-                    if (lane == 0) {
-                        acc_u += uu;
-                        acc_w += ww;
-                    }
-                }
             }
         }
     });
-    if (KE || ENERGY) {
+    if (KE) {
         const double acc_ke = warp_sum_d((double)ke_sum - (double)ke_err);
-        double wv[3] = {acc_ke, acc_u, acc_w};
-        block_partials(s, lb, wv, 3);
+        block_partials(s, lb, &acc_ke, 0, 1);
     }
 }
 
@@ -1123,7 +1100,11 @@ __device__ __forceinline__ void pair_fp64(const DevSim& s, int si, const Pos64& 
     }
 }
 
-template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+// ENERGY: per-particle energies u_i (half of each pair energy), and the energy and virial
+// partials 1 and 2.  EONLY (with ENERGY, mixed precision): the energy pass of a
+// mixed-precision handle -- the same exact integer positions and FP64 pair arithmetic,
+// but the forces stay those of the FP32 kernel (nothing is written to F or Fd).
+template <int MODE, bool ENERGY, bool KE, bool FSHIFT, bool EONLY = false>
 __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
     if (!force_selected<MODE>(s)) return;  // CTA-uniform, before any barrier
     extern __shared__ float4 smem[];
@@ -1176,7 +1157,7 @@ __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
                     }
                 }
             }
-            if (act) {
+            if (act && !EONLY) {
                 fx = -fx;
                 fy = -fy;
                 fz = -fz;
@@ -1184,9 +1165,9 @@ __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
                 s.Fd[gi] = fx;
                 s.Fd[s.npad + gi] = fy;
                 s.Fd[2 * s.npad + gi] = fz;
-                s.F[gi] = make_float4((float)fx, (float)fy, (float)fz, ENERGY ? (float)(0.5 * u) : 0.f);
-                if (ENERGY) s.ud[gi] = 0.5 * u;
+                s.F[gi] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
             }
+            if (act && ENERGY) s.ud[gi] = 0.5 * u;
             if (KE) {
                 double k = 0.0;
                 if (act) {
@@ -1211,9 +1192,12 @@ __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
         }
         __syncthreads();
     }
-    if (KE || ENERGY) {
-        double wv3[3] = {acc_ke, acc_u, acc_w};
-        block_partials(s, lb, wv3, 3);
+    if (EONLY) {
+        const double wv2[2] = {acc_u, acc_w};
+        block_partials(s, lb, wv2, 1, 2);
+    } else if (KE || ENERGY) {
+        const double wv3[3] = {acc_ke, acc_u, acc_w};
+        block_partials(s, lb, wv3, 0, 3);
     }
 }
 
@@ -1221,17 +1205,17 @@ __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
 // Each body runs for one system (DevSim by value) or, in the _many form, for the replica of
 // a batch that owns the CTA.
 
-template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+template <int MODE, bool KE, bool FSHIFT>
 __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSim s) {
-    force_body<MODE, ENERGY, KE, FSHIFT>(s, (int)blockIdx.x, (int)gridDim.x);
+    force_body<MODE, KE, FSHIFT>(s, (int)blockIdx.x, (int)gridDim.x);
 }
 
-template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+template <int MODE, bool KE, bool FSHIFT>
 __global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force_many(ManySims m) {
     __shared__ DevSim sh;
     int lb, lg;
     load_replica(m, sh, lb, lg);
-    force_body<MODE, ENERGY, KE, FSHIFT>(sh, lb, lg);
+    force_body<MODE, KE, FSHIFT>(sh, lb, lg);
 }
 
 __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build(DevSim s) {
@@ -1245,9 +1229,9 @@ __global__ void __launch_bounds__(kBW * 32, BBMD_LIST_MIN_BLOCKS) k_list_build_m
     list_build_body(sh, lb, lg);
 }
 
-template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
+template <int MODE, bool ENERGY, bool KE, bool FSHIFT, bool EONLY = false>
 __global__ void __launch_bounds__(kBW * 32) k_force64(DevSim s) {
-    force64_body<MODE, ENERGY, KE, FSHIFT>(s, (int)blockIdx.x, (int)gridDim.x);
+    force64_body<MODE, ENERGY, KE, FSHIFT, EONLY>(s, (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <int MODE, bool ENERGY, bool KE, bool FSHIFT>
@@ -1279,14 +1263,18 @@ void set_smem(K kernel) {
         g_smem_ok = false;
 }
 
+// Mixed precision: FP32 forces; an energy pass (E) adds the FP64 energy kernel, which
+// writes the per-particle energies and the energy and virial partials from exact integer
+// positions (FP32 coordinates would limit u_i to about 1e-4).
 template <int MODE, bool E, bool KE, bool FS>
 void run_force(const DevSim& s, cudaStream_t st) {
+    const size_t bytes64 = (size_t)(s.smax + 1) * sizeof(Pos64);
     if (s.precision == BBMD_PREC_FP64) {
-        size_t bytes = (size_t)(s.smax + 1) * sizeof(Pos64);
-        k_force64<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
+        k_force64<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes64, st>>>(s);
     } else {
         size_t bytes = kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
-        k_force<MODE, E, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
+        k_force<MODE, KE, FS><<<s.grid_cell, kBW * 32, bytes, st>>>(s);
+        if (E) k_force64<MODE, true, false, FS, true><<<s.grid_cell, kBW * 32, bytes64, st>>>(s);
     }
 }
 
@@ -1297,7 +1285,7 @@ void run_force_many(const ManySims& m, int total, bool fp64, int smax_max, cudaS
         k_force64_many<MODE, false, KE, FS><<<total, kBW * 32, bytes, st>>>(m);
     } else {
         size_t bytes = kStageBuffers * (size_t)(smax_max + 1) * sizeof(float4);
-        k_force_many<MODE, false, KE, FS><<<total, kBW * 32, bytes, st>>>(m);
+        k_force_many<MODE, KE, FS><<<total, kBW * 32, bytes, st>>>(m);
     }
 }
 
@@ -1320,10 +1308,12 @@ void run_force_mode(const DevSim& s, cudaStream_t st, bool energy, bool ke, bool
 
 template <int MODE, bool E, bool KE, bool FS>
 void prep_one() {
-    set_smem(k_force<MODE, E, KE, FS>);
     set_smem(k_force64<MODE, E, KE, FS>);
-    if (!E) {
-        set_smem(k_force_many<MODE, E, KE, FS>);
+    if (E) {
+        if (!KE) set_smem(k_force64<MODE, true, false, FS, true>);
+    } else {
+        set_smem(k_force<MODE, KE, FS>);
+        set_smem(k_force_many<MODE, KE, FS>);
         set_smem(k_force64_many<MODE, E, KE, FS>);
     }
 }
@@ -1360,7 +1350,7 @@ int force_blocks_per_sm(const DevSim& s) {
     if (s.precision == BBMD_PREC_FP64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force64<0, false, true, false>, kBW * 32, bytes);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force<0, false, true, false>, kBW * 32, bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force<0, true, false>, kBW * 32, bytes);
     return nb > 0 ? nb : 1;
 }
 

@@ -82,7 +82,8 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
     const float vtofix = pow2f(kVelExp);
     const float dtx = dtf * pow2f(s.kexp > 126 ? 126 : s.kexp);  // k <= 61 in practice
     const int lane = threadIdx.x & 31;
-    const float half_thr = 0.5f * s.disp_thr;
+    const float half_thr =
+        0.5f * (s.nbr_mode == BBMD_NBR_VERLET ? fminf(s.disp_thr, s.disp_far) : s.disp_far);
     bool near = false;
     for (int64_t base = lb * (int64_t)blockDim.x + (threadIdx.x & ~31); base < s.n;
          base += (int64_t)lg * blockDim.x) {
@@ -182,14 +183,27 @@ __global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
     integrate_body<FP64>(s, (int)blockIdx.x, (int)gridDim.x);
 }
 
-// Rebuild trigger.  A pair missing from the lists (or a neighbour outside the cell stencil,
-// in cell mode) can interact only if its two particles moved, since the build, by more
-// than the skin together, and both lie in the same or neighbouring build cells.  So the
-// lists stay valid while, for every build cell c, the sum of its two largest displacements
-// and the sum of its largest with the largest of each of its 26 neighbours stay within
-// the skin.  Pass 1 finds the two largest displacements of every cell (a warp per cell,
-// the particles of a cell being contiguous); pass 2 checks the sums, starting only from
-// cells whose largest displacement exceeds half the threshold.
+// Rebuild trigger.  Since the last build, a pair (i, j) has come closer by at most
+// d_i + d_j, the sum of the two displacements.  Two kinds of pairs could start to interact
+// unseen:
+//   (1) Verlet mode: a pair of the same or of neighbouring build cells that the list left
+//       out.  Its distance at the build was at least rc_ab + skin, so it interacts only
+//       after closing more than the skin.
+//   (2) Both modes: a pair whose build cells are two or more apart along some axis.  One
+//       whole cell of side D lies between them, so they were more than D_min apart (the
+//       smallest side over the axes) and interact only after closing more than
+//       D_min - rc_max, where rc_max is the largest cutoff.  The cell grid makes
+//       D_min >= rc_max + skin, but by little when the cells just fit.
+// Rule (1) compares, for every build cell, its two largest displacements, and its largest
+// with the largest of each of its 26 neighbours, with the skin.  Rule (2) compares the two
+// largest displacements of the whole system with D_min - rc_max.  Both thresholds carry a
+// relative margin of 1e-4 against the FP32 rounding of the displacements.  Cell mode
+// evaluates every pair of the 27 build cells at every step, so only rule (2) applies there.
+// Pass 1 finds the two largest displacements of every cell (a warp per cell, the particles
+// of a cell being contiguous) and of every CTA's cells (partials 6 and 7); pass 2 applies
+// rule (1) from the cells whose largest displacement exceeds half the skin, and its CTA 0
+// merges the CTA pairs of pass 1 for rule (2).  Both passes run only in steps where some
+// displacement exceeds half of the smaller threshold.
 __device__ __forceinline__ void top2_insert(float v, float& a, float& b) {
     if (v > a) {
         b = a;
@@ -199,52 +213,87 @@ __device__ __forceinline__ void top2_insert(float v, float& a, float& b) {
     }
 }
 
+__device__ __forceinline__ void warp_top2(float& a, float& b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oa = __shfl_xor_sync(FULL, a, o);
+        const float ob = __shfl_xor_sync(FULL, b, o);
+        top2_insert(oa, a, b);
+        top2_insert(ob, a, b);
+    }
+}
+
+constexpr int kTopQ = 6;  // partials 6 and 7: the two largest displacements of each CTA
+
 __device__ __forceinline__ void celltop_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->near) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nwarps = (int64_t)lg * (blockDim.x >> 5);
+    float wa = 0.f, wb = 0.f;  // the warp's two largest over its cells
     for (int64_t c = (lb * (int64_t)blockDim.x + threadIdx.x) >> 5; c < s.ncell; c += nwarps) {
         const int st = s.cell_start[c], en = s.cell_start[c + 1];
         float a = 0.f, b = 0.f;
         for (int k = st + lane; k < en; k += 32) top2_insert(s.disp[k], a, b);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oa = __shfl_xor_sync(FULL, a, o);
-            const float ob = __shfl_xor_sync(FULL, b, o);
-            top2_insert(oa, a, b);
-            top2_insert(ob, a, b);
-        }
+        warp_top2(a, b);
         if (lane == 0) s.mtop[c] = make_float2(a, b);
+        top2_insert(a, wa, wb);
+        top2_insert(b, wa, wb);
+    }
+    __shared__ float2 red[kThreads / 32];
+    if (lane == 0) red[w] = make_float2(wa, wb);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f, b = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            top2_insert(red[k].x, a, b);
+            top2_insert(red[k].y, a, b);
+        }
+        s.partials[kTopQ * kMaxPartials + lb] = a;
+        s.partials[(kTopQ + 1) * kMaxPartials + lb] = b;
     }
 }
 
+// Pass 1 ran on grid_part CTAs (of the system, or of its replica in a batch launch).
 __device__ __forceinline__ void check_body(const DevSim& s, int lb, int lg) {
     DevScalars* sc = s.sc;
     if (!sc->near) return;
-    const float thr = s.disp_thr;
     bool need = false;
-    for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < s.ncell;
-         c += (int64_t)lg * blockDim.x) {
-        const float2 m = s.mtop[c];
-        if (m.x <= 0.5f * thr) continue;
-        float mx = m.y;  // the cell's own second largest
-        int a[3];
-        cell_coords((int)c, s.nc, a[0], a[1], a[2]);
-        for (int dz = -1; dz <= 1; ++dz) {
-            int z = a[2] + dz;
-            z = z < 0 ? z + s.nc[2] : (z >= s.nc[2] ? z - s.nc[2] : z);
-            for (int dy = -1; dy <= 1; ++dy) {
-                int y = a[1] + dy;
-                y = y < 0 ? y + s.nc[1] : (y >= s.nc[1] ? y - s.nc[1] : y);
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if ((dx | dy | dz) == 0) continue;
-                    int x = a[0] + dx;
-                    x = x < 0 ? x + s.nc[0] : (x >= s.nc[0] ? x - s.nc[0] : x);
-                    mx = fmaxf(mx, s.mtop[(z * s.nc[1] + y) * s.nc[0] + x].x);
+    if (lb == 0 && threadIdx.x < 32) {
+        // rule (2): the two largest displacements of the system
+        float a = 0.f, b = 0.f;
+        for (int k = threadIdx.x; k < s.grid_part; k += 32) {
+            top2_insert((float)s.partials[kTopQ * kMaxPartials + k], a, b);
+            top2_insert((float)s.partials[(kTopQ + 1) * kMaxPartials + k], a, b);
+        }
+        warp_top2(a, b);
+        if (a + b > s.disp_far) need = true;
+    }
+    if (s.nbr_mode == BBMD_NBR_VERLET) {
+        // rule (1)
+        const float thr = s.disp_thr;
+        for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < s.ncell;
+             c += (int64_t)lg * blockDim.x) {
+            const float2 m = s.mtop[c];
+            if (m.x <= 0.5f * thr) continue;
+            float mx = m.y;  // the cell's own second largest
+            int a[3];
+            cell_coords((int)c, s.nc, a[0], a[1], a[2]);
+            for (int dz = -1; dz <= 1; ++dz) {
+                int z = a[2] + dz;
+                z = z < 0 ? z + s.nc[2] : (z >= s.nc[2] ? z - s.nc[2] : z);
+                for (int dy = -1; dy <= 1; ++dy) {
+                    int y = a[1] + dy;
+                    y = y < 0 ? y + s.nc[1] : (y >= s.nc[1] ? y - s.nc[1] : y);
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if ((dx | dy | dz) == 0) continue;
+                        int x = a[0] + dx;
+                        x = x < 0 ? x + s.nc[0] : (x >= s.nc[0] ? x - s.nc[0] : x);
+                        mx = fmaxf(mx, s.mtop[(z * s.nc[1] + y) * s.nc[0] + x].x);
+                    }
                 }
             }
+            if (m.x + mx > thr) need = true;
         }
-        if (m.x + mx > thr) need = true;
     }
     if (need) sc->rebuild = 1;
 }
@@ -419,8 +468,12 @@ __device__ __forceinline__ long long quantize_dev(double x, int k, long long L) 
     return q;
 }
 
+// FCC site i (4 m^3 sites): ((ix, iy, iz) + basis_b + 1/4) L/m, then, when jitter > 0,
+// coordinate d moved by jitter (2u - 1) with u the uniform draw 3i + d of stream 5 (the
+// same IEEE operations as the Python generator: no fused multiply-add).
 __global__ void __launch_bounds__(kThreads) k_init_fcc(DevSim s, int m, double Lx, double Ly,
-                                                      double Lz) {
+                                                      double Lz, double jitter,
+                                                      unsigned long long seed) {
     const double bx[4] = {0.0, 0.5, 0.5, 0.0}, by[4] = {0.0, 0.5, 0.0, 0.5},
                  bz[4] = {0.0, 0.0, 0.5, 0.5};
     double ax = Lx / m, ay = Ly / m, az = Lz / m;
@@ -429,9 +482,17 @@ __global__ void __launch_bounds__(kThreads) k_init_fcc(DevSim s, int m, double L
         int b = (int)(i & 3);
         int64_t cidx = i >> 2;
         int64_t ix = cidx % m, iy = (cidx / m) % m, iz = cidx / ((int64_t)m * m);
-        double px = ((double)ix + bx[b] + 0.25) * ax;
-        double py = ((double)iy + by[b] + 0.25) * ay;
-        double pz = ((double)iz + bz[b] + 0.25) * az;
+        double p3[3] = {((double)ix + bx[b] + 0.25) * ax, ((double)iy + by[b] + 0.25) * ay,
+                        ((double)iz + bz[b] + 0.25) * az};
+        if (jitter > 0.0) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const unsigned long long z = draw(seed, 5, 3ull * (unsigned long long)i + d);
+                const double u = (double)(z >> 11) * 0x1p-53;
+                p3[d] = __dadd_rn(p3[d], __dmul_rn(jitter, __dsub_rn(__dmul_rn(2.0, u), 1.0)));
+            }
+        }
+        const double px = p3[0], py = p3[1], pz = p3[2];
         s.x[i] = (uint64_t)quantize_dev(px, s.kexp, s.Lfix[0]);
         s.x[s.npad + i] = (uint64_t)quantize_dev(py, s.kexp, s.Lfix[1]);
         s.x[2 * s.npad + i] = (uint64_t)quantize_dev(pz, s.kexp, s.Lfix[2]);
@@ -873,10 +934,11 @@ void launch_reduce_partials(const DevSim& s, cudaStream_t st, int nq, double* ou
     k_reduce_partials<<<1, 256, 0, st>>>(s, nb, q, out_dev, 0);
 }
 
-void launch_init_fcc(const DevSim& s, cudaStream_t st, int m) {
+void launch_init_fcc(const DevSim& s, cudaStream_t st, int m, double jitter, uint64_t seed) {
     k_init_fcc<<<s.grid_part, kThreads, 0, st>>>(s, m, ldexp((double)s.Lfix[0], -s.kexp),
                                                  ldexp((double)s.Lfix[1], -s.kexp),
-                                                 ldexp((double)s.Lfix[2], -s.kexp));
+                                                 ldexp((double)s.Lfix[2], -s.kexp), jitter,
+                                                 (unsigned long long)seed);
 }
 
 void launch_init_mb(const DevSim& s, cudaStream_t st, double T0, uint64_t seed, double* tmp3) {

@@ -72,7 +72,7 @@ class StandinSim:
 
     def observe(self, mask, nbins=500, rmax=5.0, k=7.25):
         return {"temperature": 1.0, "pe": -5.0 * self.n, "ke": 1.5 * self.n, "xi": 0.0,
-                "step": self.steps}
+                "step": self.steps, "n_rebuilds": self.steps // 5}
 
     def get_state(self, out=None):
         if out is None:
@@ -110,10 +110,12 @@ def main():
     bbmd.load = lambda *a, **k: None
     bbmd.Sim = StandinSim
     bbmd.Batch = StandinBatch
+    bbmd.fma_peak = lambda precision=0: (80.0 if precision == 0 else 1.2, 152)
     torch.cuda.Event = StandinEvent
     torch.cuda.Stream = StandinStream
     torch.cuda.synchronize = lambda *a, **k: None
     torch.cuda.current_device = lambda: 0
+    torch.cuda.get_device_properties = lambda dev: type("Props", (), {"multi_processor_count": 152})
     torch.cuda.empty_cache = lambda: None
     empty = torch.empty
     torch.empty = lambda *a, **k: empty(*a, **{key: v for key, v in k.items()

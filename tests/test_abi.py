@@ -32,7 +32,7 @@ def test_params_struct_layout_matches_header():
     from paper_1105_5613_gb300 import bbmd
 
     # 4 int32 + 3*4 doubles + 2 doubles + 1 double + 2 int32
-    assert ctypes.sizeof(bbmd.bbmd_params) == 16 + 12 * 8 + 2 * 8 + 8 + 16
+    assert ctypes.sizeof(bbmd.bbmd_params) == 16 + 12 * 8 + 2 * 8 + 8 + 16 + 8
     p = bbmd.ka_params()
     assert p.eps[0][1] == 1.5 and p.sigma[1][1] == 0.88 and p.rcut[0][1] == 2.0
 

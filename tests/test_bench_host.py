@@ -49,14 +49,14 @@ def test_force_counters_follow_the_source(bench, tmp_path, monkeypatch):
     _fake_tree(tmp_path, src, rec)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.force_traffic(1000) == pytest.approx(284000.0)
-    issue = bench.force_issue(1_000_000, 1.0, 4, 2000.0)
+    issue = bench.force_issue(1_000_000, 1.0, 4, 2000.0, 152)
     # 150e6 warp instructions in 1 ms against 152 SMs x 4 per cycle at 2 GHz
     assert issue["frac"] == pytest.approx(1.5e11 / (152 * 4 * 2e9))
-    assert bench.force_issue(1_000_000, 1.0, 8, 2000.0) is None  # another block shape
+    assert bench.force_issue(1_000_000, 1.0, 8, 2000.0, 152) is None  # another block shape
     # any change of the source voids the record
     (tmp_path / "paper_1105_5613_gb300" / "csrc" / "k_force.cu").write_text(src + " ")
     assert bench.force_traffic(1000) is None
-    assert bench.force_issue(1_000_000, 1.0, 4, 2000.0) is None
+    assert bench.force_issue(1_000_000, 1.0, 4, 2000.0, 152) is None
 
 
 def test_a_failing_secondary_leg_is_reported_not_fatal(bench):
@@ -87,8 +87,10 @@ def test_bench_runs_end_to_end_against_standins():
               "roofline", "cpu_baseline", "gpu_launches"):
         assert k in d, k
     assert d["gpu_launches"] == 3 * 16 + 2
-    for leg in ("fp64", "soft_sphere", "replicas", "large", "cpu_baseline"):
+    for leg in ("fp64", "soft_sphere", "replicas", "large", "cpu_baseline", "fma_probe"):
         assert "error" not in d[leg], d[leg]
+    assert d["roofline"]["peak"] == d["fma_probe"]["fp32_tflops"]
+    assert {"roofline", "phases_ms_per_step", "rebuilds_per_step"} <= set(d["large"]["mixed"])
     assert {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"} <= set(d["e2e"])
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(d["roofline"])
     assert {"value", "unit", "cores", "kind", "sample"} <= set(d["cpu_baseline"])
@@ -113,4 +115,6 @@ def test_reference_arm_prints_its_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert "workload" in d["config"]
+    # the config names the bounded sample this arm times, and what it is a sample of
+    assert d["config"]["n_particles"] == 4 * 20 ** 3
+    assert "N=32000" in d["config"]["workload"] and "sample_of" in d["config"]

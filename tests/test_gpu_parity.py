@@ -1,8 +1,10 @@
 """GPU-vs-oracle parity through the C ABI (libbbmd.so), on seeded generator inputs.
 
 Bars: cells and Verlet neighbour sets bit-exact; mixed-precision forces e_i <= 1e-5
-(median) and <= 1e-4 (max); potential energy per particle within 1e-6; 100-step position
-RMS <= 1e-4; the FP64 form within 1e-10 relative per force."""
+(median) and <= 1e-4 (max); potential energy of every particle within 1e-6 absolute (the
+energy pass evaluates pair energies in FP64 from the exact integer positions, so the
+tests hold 1e-9); 100-step position RMS <= 1e-4; the FP64 form within 1e-10 relative per
+force."""
 import numpy as np
 import pytest
 
@@ -26,11 +28,22 @@ def _lib():
     bbmd.load()
 
 
-def make(ncell=10, seed=0, T=2.0, shake=0.1, **kw):
+def make(ncell=10, seed=0, T=2.0, shake=0.1, rc_all=None, **kw):
+    """rc_all: one cutoff for every species pair (the glass study of Sec. 4 uses 1.2)."""
     n, L, pos, vel, sp = mixture(ncell, seed=seed, T=T, shake=shake)
     p = bbmd.ka_params(**kw)
+    if rc_all is not None:
+        for a in range(2):
+            for b in range(2):
+                p.rcut[a][b] = rc_all
     sim = bbmd.Sim(p, n, L, sp, pos, vel)
     return sim, n, L, pos, vel, sp, p
+
+
+# (potential, truncation, one cutoff for every pair or None for 2.5 sigma_ab): the
+# benchmark mixture, and the soft-sphere shifted-force model of Sec. 2.1 at 2.5 sigma_ab
+# and at the glass run's r_c = 1.2 (Sec. 4)
+MODELS = [(0, 1, None), (1, 2, None), (1, 2, 1.2)]
 
 
 # ------------------------------------------------------------------- binning / lists ----
@@ -61,11 +74,12 @@ def test_neighbor_sets_bit_exact(ncell, shake):
 
 # ---------------------------------------------------------------------------- forces ----
 
-@pytest.mark.parametrize("pot,shift", [(0, 1), (0, 0), (0, 2), (1, 1)])
+@pytest.mark.parametrize("pot,shift,rc_all", [(0, 1, None), (0, 0, None), (0, 2, None),
+                                             (1, 1, None), (1, 2, None), (1, 2, 1.2)])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_forces_mixed(pot, shift, mode):
+def test_forces_mixed(pot, shift, rc_all, mode):
     sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.12, potential=pot, shift=shift,
-                                      nbr_mode=mode)
+                                      nbr_mode=mode, rc_all=rc_all)
     xq, _, _ = quantized(pos, L)
     po = oracle_params(p)
     Fo, uo, Wo, PEo = oracle.forces(xq, sp, L, po)
@@ -75,18 +89,21 @@ def test_forces_mixed(pot, shift, mode):
     obs = sim.observe(bbmd.OBS_ENERGY | bbmd.OBS_VIRIAL)
     assert abs(obs["pe"] - PEo) / n <= 1e-6
     assert abs(obs["virial"] - Wo) <= 1e-6 * abs(Wo)
-    # per-particle energies: FP32 pair energies, FP64 sums
-    assert np.abs(u - uo).max() <= 2e-4
+    # per-particle energies: the bar is 1e-6 absolute; the FP64 energy pass reaches
+    # rounding level
+    assert np.abs(u - uo).max() <= 1e-9, np.abs(u - uo).max()
     sim.close()
 
 
 @pytest.mark.parametrize("ncell", [8, 10])
-@pytest.mark.parametrize("shift", [1, 2])
+@pytest.mark.parametrize("pot,shift,rc_all", [(0, 1, None), (0, 2, None), (1, 2, None),
+                                             (1, 2, 1.2)])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_forces_fp64_form(shift, mode, ncell):
+def test_forces_fp64_form(pot, shift, rc_all, mode, ncell):
     # ncell 10: L * 2^k close to 2^62 and an odd number of cells per axis
     sim, n, L, pos, vel, sp, p = make(ncell=ncell, shake=0.12, precision=bbmd.PREC_FP64,
-                                      shift=shift, nbr_mode=mode)
+                                      potential=pot, shift=shift, nbr_mode=mode,
+                                      rc_all=rc_all)
     xq, _, _ = quantized(pos, L)
     po = oracle_params(p)
     Fo, uo, Wo, PEo = oracle.forces(xq, sp, L, po)
@@ -167,9 +184,12 @@ def test_trajectory_split_calls_equal_one_call():
     b.close()
 
 
+@pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("prec,tol", [(0, 1e-4), (1, 1e-9)])
-def test_trajectory_nose_hoover_100_steps(prec, tol):
-    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.0, T=2.0, precision=prec)
+def test_trajectory_nose_hoover_100_steps(prec, tol, model):
+    pot, shift, rc_all = model
+    sim, n, L, pos, vel, sp, p = make(ncell=10, shake=0.0, T=2.0, precision=prec,
+                                      potential=pot, shift=shift, rc_all=rc_all)
     xq, _, _ = quantized(pos, L)
     st = oracle.MDState(xq, vel, sp, L, oracle_params(p))
     th = (0.5, 0.5, 0.5)
@@ -223,6 +243,55 @@ def test_gr_counts_bit_exact(ncell):
     assert np.array_equal(o["gr_counts"], ref)
     g = oracle.gr_normalize(ref, sp, L, 5.0)
     assert np.allclose(o["gr"], g, rtol=1e-12, atol=1e-12)
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_msd_fs_per_particle_displacements(prec):
+    """Every particle moved by its own seeded displacement, B particles by larger ones and
+    some particles by more than a box length (image counters through several boxes):
+    per-species MSD and F_s(k, t) equal the oracle's on the same positions and counters."""
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.1, precision=prec)
+    xq0, _, _ = quantized(pos, L)
+    sim.observe(bbmd.OBS_SET_REF)
+    rng = np.random.default_rng(41)
+    disp = rng.normal(0.0, 0.4, (n, 3))
+    disp[sp == 1] *= 3.0
+    far = rng.choice(n, 60, replace=False)
+    disp[far] += rng.choice([-1.0, 1.0], (60, 3)) * rng.uniform(1.0, 3.5, (60, 3)) * L
+    moved = xq0 + disp
+    img = np.floor(moved / L).astype(np.int32)
+    wrapped = moved - L * img
+    sim.set_state(wrapped, vel, img)
+    gp, _, gi = sim.get_state()
+    assert np.array_equal(gi, img)
+    xq1, _, _ = quantized(wrapped, L)
+    assert np.array_equal(gp, xq1)
+    for kv in (7.25, 3.1):
+        o = sim.observe(bbmd.OBS_MSD | bbmd.OBS_FS, k=kv)
+        msd, fs = oracle.msd_fs(xq1, img, xq0, np.zeros_like(img), sp, L, kv)
+        assert np.allclose(o["msd"], msd, rtol=1e-12, atol=0), (o["msd"], msd)
+        assert np.allclose(o["fs"], fs, rtol=1e-12, atol=1e-13), (o["fs"], fs)
+    assert abs(msd[1] - msd[0]) > 0.1 * msd[0]  # the species averages are told apart
+    sim.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 2e-3), (1, 1e-7)])
+def test_msd_fs_after_200_steps(prec, tol):
+    """200 Nose-Hoover steps from the same start through the library and the oracle:
+    per-species MSD and F_s(k = 7.25, t) agree to the trajectory's own precision."""
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.05, T=2.0, precision=prec)
+    xq, _, _ = quantized(pos, L)
+    st = oracle.MDState(xq, vel, sp, L, oracle_params(p))
+    sim.observe(bbmd.OBS_SET_REF)
+    th = (1.5, 1.5, 0.5)
+    sim.step(200, 0.005, (bbmd.THERMO_NH, *th))
+    oracle.md_run(st, 200, 0.005, thermo=th, use_cells=True)
+    o = sim.observe(bbmd.OBS_MSD | bbmd.OBS_FS)
+    msd, fs = oracle.msd_fs(st.pos, st.image, xq, np.zeros((n, 3), np.int32), sp, L, 7.25)
+    assert np.allclose(o["msd"], msd, rtol=tol), (o["msd"], msd)
+    assert np.allclose(o["fs"], fs, rtol=0, atol=tol), (o["fs"], fs)
+    assert msd.min() > 0.05  # the particles did move
     sim.close()
 
 
@@ -446,15 +515,18 @@ def test_minimize_matches_oracle():
     sim.close()
 
 
-def test_device_generated_initial_state_matches_generator():
+@pytest.mark.parametrize("jitter", [0.0, 0.07])
+def test_device_generated_initial_state_matches_generator(jitter):
     ncell = 9
     n = 4 * ncell ** 3
     L = gen.box_for(n, 1.2)
     sp = gen.assign_species(n, n // 5, 4)
-    sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, None, None, T0=1.5, seed=4)
+    sim = bbmd.Sim(bbmd.ka_params(init_jitter=jitter), n, L, sp, None, None, T0=1.5, seed=4)
     gp, gv, _ = sim.get_state()
-    xq, _, _ = quantized(gen.fcc_lattice(ncell, L), L)
+    xq, _, _ = quantized(gen.fcc_sites(ncell, L, np.arange(n), jitter=jitter, seed=4), L)
     assert np.array_equal(gp, xq)
+    if jitter == 0.0:
+        assert np.array_equal(xq, quantized(gen.fcc_lattice(ncell, L), L)[0])
     ref = gen.maxwell_boltzmann(n, 1.5, 4, np.ones(n))
     assert np.abs(gv - ref).max() < 1e-12
     sim.close()

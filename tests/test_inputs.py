@@ -63,3 +63,18 @@ def test_fcc_sites_equal_the_lattice():
     full = gen.fcc_lattice(9, L)
     idx = np.random.default_rng(0).permutation(full.shape[0])[:500]
     assert np.array_equal(gen.fcc_sites(9, L, idx), full[idx])
+
+
+def test_fcc_jitter_is_bounded_seeded_and_counter_addressed():
+    ncell, L = 6, gen.box_for(4 * 6 ** 3, 1.2)
+    n = 4 * ncell ** 3
+    idx = np.arange(n)
+    base = gen.fcc_sites(ncell, L, idx)
+    a = gen.fcc_sites(ncell, L, idx, jitter=0.05, seed=3)
+    d = a - base
+    assert np.abs(d).max() <= 0.05 and np.abs(d).max() > 0.045
+    assert abs(d.mean()) < 0.005  # centred
+    # the same draws whatever subset is asked for (counter-based), another seed differs
+    sub = np.array([5, 17, n - 1])
+    assert np.array_equal(gen.fcc_sites(ncell, L, sub, jitter=0.05, seed=3), a[sub])
+    assert not np.array_equal(gen.fcc_sites(ncell, L, idx, jitter=0.05, seed=4), a)

@@ -76,3 +76,20 @@ def test_noalloc_rejects_oversize():
     sim.step(2, 0.005)
     assert np.isfinite(sim.observe(bbmd.OBS_ENERGY)["pe"])
     sim.close()
+
+
+def test_calls_use_the_handles_device():
+    """A handle works on the device it was created on, whatever device the caller has
+    current, and the caller's device is current again after the call.  Needs two GPUs."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.device_count() < 2:
+        pytest.skip("a single device: nothing to switch to")
+    with torch.cuda.device(0):
+        sim = _sim(12, 0.05)
+        ref = sim.observe(bbmd.OBS_GR)["gr_counts"]
+    with torch.cuda.device(1):
+        got = sim.gr_counts_noalloc()
+        again = sim.observe(bbmd.OBS_GR)["gr_counts"]
+        assert torch.cuda.current_device() == 1
+    sim.close()
+    assert np.array_equal(got, ref) and np.array_equal(again, ref)

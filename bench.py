@@ -551,8 +551,11 @@ def fma_probe(bbmd, gpu=None):
     with clk:
         f32, nsm = bbmd.fma_peak(bbmd.PREC_MIXED)
         f64, _ = bbmd.fma_peak(bbmd.PREC_FP64)
+        # shared-memory scatter-adds (the reaction update of a half-list kernel)
+        scatter = {name: bbmd.smem_scatter_rate(kind)
+                   for kind, name in ((0, "fixed64_from_f32"), (1, "u32"), (2, "f32"))}
     return {"fp32_tflops": f32, "fp64_tflops": f64, "sm_count": nsm,
-            "clocks": clk.summary()}
+            "smem_scatter_adds_per_s": scatter, "clocks": clk.summary()}
 
 
 def ctypes_sizeof_obs(bbmd):

@@ -362,6 +362,16 @@ const char* bbmd_last_error(const bbmd_sim* sim);
  * for the duration of the call; synchronising; about half a second. */
 bbmd_status bbmd_fma_peak(int32_t precision, int32_t* sm_count, double* tflops);
 
+/* Measured rate of shared-memory scatter-adds on the current device, in adds per second
+ * over the whole GPU: kind 0 = 64-bit integer adds of a float converted to 2^32 fixed
+ * point (the deterministic reaction update of a half-list force kernel), 1 = 32-bit
+ * integer adds, 2 = FP32 adds.  Each thread of 4 CTAs of 256 threads per SM adds at
+ * addresses that differ across a warp's lanes (no bank conflicts: the most favourable
+ * case); best of 3 timed launches after a warm-up.  A measurement helper behind the
+ * choice of a full Verlet list; the paper has no counterpart.  Allocates a few bytes of
+ * device memory for the duration of the call; synchronising. */
+bbmd_status bbmd_smem_scatter_rate(int32_t kind, double* adds_per_s);
+
 #ifdef __cplusplus
 }
 #endif

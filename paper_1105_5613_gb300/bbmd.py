@@ -89,7 +89,7 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_get_forces_ids", "bbmd_create_batch", "bbmd_step_batch",
            "bbmd_batch_replica", "bbmd_batch_size", "bbmd_batch_set_branches",
            "bbmd_destroy_batch",
-           "bbmd_batch_last_error", "bbmd_fma_peak"]
+           "bbmd_batch_last_error", "bbmd_fma_peak", "bbmd_smem_scatter_rate"]
 
 _lib = None
 
@@ -160,6 +160,8 @@ def load(path: str | None = None):
     L.bbmd_last_error.restype = C.c_char_p
     L.bbmd_fma_peak.argtypes = [C.c_int32, P(C.c_int32), P(d)]
     L.bbmd_fma_peak.restype = C.c_int
+    L.bbmd_smem_scatter_rate.argtypes = [C.c_int32, P(d)]
+    L.bbmd_smem_scatter_rate.restype = C.c_int
     _lib = L
     return L
 
@@ -204,6 +206,14 @@ def fma_peak(precision=PREC_MIXED):
     tf = C.c_double(0.0)
     _check(None, L.bbmd_fma_peak(precision, C.byref(nsm), C.byref(tf)))
     return tf.value, nsm.value
+
+
+def smem_scatter_rate(kind):
+    """Measured shared-memory scatter-adds per second of the current device (kind 0: 64-bit
+    fixed point from float, 1: 32-bit integer, 2: FP32)."""
+    r = C.c_double(0.0)
+    _check(None, load().bbmd_smem_scatter_rate(kind, C.byref(r)))
+    return r.value
 
 
 def torch_allocator(device=None):

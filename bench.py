@@ -504,7 +504,8 @@ def run_replicas(args, stream):
     """Batched replicas: args.replicas mixtures of uneven size N_r in [2048, 32768] (multiples
     of 5), random sequential addition (d_min = 0.7) relaxed by 200 steepest-descent steps,
     temperatures evenly spaced in [0.4, 2.0], Nose-Hoover (tau = 0.5), dt = 0.005; all
-    replicas advanced by one graph launch per step (bbmd_step_batch)."""
+    replicas advanced by the persistent kernel, one launch for the timed steps
+    (bbmd_step_batch)."""
     import torch
 
     from inputs import generate as gen
@@ -532,11 +533,15 @@ def run_replicas(args, stream):
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     shapes = sorted({b.replica(r).info()["block_z"] for r in range(R)})
+    path = "persistent" if b.uses_persistent() else "graph"
     Ts = [b.replica(r).observe(bbmd.OBS_ENERGY)["temperature"] for r in (0, R - 1)]
     b.close()
     ntot = sum(ns)
     return {"workload": f"{R} replicas, N_r in [2048, 32768] (sum {ntot}), RSA + 200 SD steps, "
-                        "T_r = 0.4 .. 2.0, Nose-Hoover, dt=0.005, one graph launch per step",
+                        "T_r = 0.4 .. 2.0, Nose-Hoover, dt=0.005, "
+                        + ("one persistent kernel launch per call (up to 1024 steps)"
+                           if path == "persistent" else "one graph launch per step"),
+            "path": path,
             "value": ntot * args.replica_steps / (ms / 1e3), "unit": "particle-steps/s",
             "steps": args.replica_steps, "ms_per_step": ms / args.replica_steps,
             "n_total": ntot, "block_z_used": shapes, "generate_s": t_gen, "setup_s": t_setup,

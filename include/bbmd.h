@@ -282,13 +282,15 @@ bbmd_status bbmd_get_info(const bbmd_sim* sim, bbmd_info* info);
 /* ---- Replica batches --------------------------------------------------------------
  * Many independent systems ("replicas": e.g. one mixture per temperature, of uneven sizes)
  * advanced together.  Each replica is a complete handle with its own box, particles,
- * cells, lists, block shape and thermostat variables; bbmd_step_batch advances all of them
- * with one CUDA graph launch per step: groups of replicas on parallel branches of that
- * graph, one kernel launch per phase covering every replica of a group.  The paper runs one system at a time (Sec. 3, 4); a batch fills the GPU with
+ * cells, lists and thermostat variables; bbmd_step_batch advances all of them with one
+ * persistent kernel launch for up to 1024 steps (bbmd_batch_set_mode) or one CUDA graph
+ * launch per step: groups of replicas on parallel branches of that graph, one kernel
+ * launch per phase covering every replica of a group.  The paper runs one system at a time (Sec. 3, 4); a batch fills the GPU with
  * systems far smaller than it. */
 typedef struct bbmd_batch bbmd_batch;
 
-/* Create n_rep >= 1 replicas sharing params.  Replica r: n[r] particles in the box
+/* Create n_rep >= 1 replicas sharing params (and one block shape: params.block_z, 0 for
+ * 2 x 2 x 4).  Replica r: n[r] particles in the box
  * box[3r .. 3r+2]; species[r] (host, n[r] labels, required); positions pos[r] and
  * velocities vel[r] as in bbmd_create (pos or vel NULL, or an entry NULL, for the
  * device-generated FCC lattice / Maxwell-Boltzmann velocities at T0[r] under seed + r).
@@ -317,6 +319,24 @@ int32_t bbmd_batch_size(const bbmd_batch* b);
  * groups of about equal particle count; within a group one launch per phase covers every
  * replica, and the groups run concurrently.  Takes effect at the next bbmd_step_batch. */
 bbmd_status bbmd_batch_set_branches(bbmd_batch* b, int32_t branches);
+
+/* Step path of a batch.  AUTO (the default): the persistent step when it applies, else the
+ * graph.  PERSISTENT: one cooperative kernel launch runs up to 1024 whole steps of every
+ * replica.  Each phase of a replica's step (integrate, rebuild trigger, the gated sort
+ * chain and list build, forces, finalize) is cut into work items with the CTA index and
+ * count of the per-replica kernels, so the states are bit for bit those of stepping each
+ * replica alone.  All resident CTAs take the items from one queue, step after step and
+ * phase after phase; an item starts once its replica's previous phase has finished, so
+ * the phases and steps of different replicas overlap.  It applies to mixed precision with
+ * block shape 2 x 2 x 4 (the batch default) on a device with cooperative launch;
+ * otherwise bbmd_step_batch returns BBMD_ERR_STATE.  A wait gives up after a second; the
+ * replicas then report BBMD_ERR_TIMEOUT at their next synchronising call.  GRAPH: one
+ * CUDA graph launch per step (bbmd_batch_set_branches). */
+enum { BBMD_BATCH_AUTO = 0, BBMD_BATCH_GRAPH = 1, BBMD_BATCH_PERSISTENT = 2 };
+bbmd_status bbmd_batch_set_mode(bbmd_batch* b, int32_t mode);
+
+/* 1 if the next bbmd_step_batch takes the persistent step, else 0. */
+int32_t bbmd_batch_uses_persistent(const bbmd_batch* b);
 
 /* Release every replica and the batch (NULL is ignored). */
 void bbmd_destroy_batch(bbmd_batch* b);

@@ -26,6 +26,7 @@ PREC_MIXED, PREC_FP64 = 0, 1
 NBR_VERLET, NBR_CELL = 0, 1
 THERMO_NVE, THERMO_NH = 0, 1
 OBS_ENERGY, OBS_VIRIAL, OBS_MOMENTUM, OBS_GR, OBS_MSD, OBS_FS, OBS_SET_REF = 1, 2, 4, 8, 16, 32, 64
+BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 
 
 class BBMDError(RuntimeError):
@@ -88,6 +89,7 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error",
            "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_get_forces_ids", "bbmd_create_batch", "bbmd_step_batch",
            "bbmd_batch_replica", "bbmd_batch_size", "bbmd_batch_set_branches",
+           "bbmd_batch_set_mode", "bbmd_batch_uses_persistent",
            "bbmd_destroy_batch",
            "bbmd_batch_last_error", "bbmd_fma_peak", "bbmd_smem_scatter_rate"]
 
@@ -150,6 +152,10 @@ def load(path: str | None = None):
     L.bbmd_batch_replica.restype = vp
     L.bbmd_batch_set_branches.argtypes = [vp, C.c_int32]
     L.bbmd_batch_set_branches.restype = C.c_int
+    L.bbmd_batch_set_mode.argtypes = [vp, C.c_int32]
+    L.bbmd_batch_set_mode.restype = C.c_int
+    L.bbmd_batch_uses_persistent.argtypes = [vp]
+    L.bbmd_batch_uses_persistent.restype = C.c_int32
     L.bbmd_batch_size.argtypes = [vp]
     L.bbmd_batch_size.restype = C.c_int32
     L.bbmd_destroy_batch.argtypes = [vp]
@@ -490,6 +496,16 @@ class Batch:
         rc = load().bbmd_batch_set_branches(self.h, int(k))
         if rc != BBMD_OK:
             raise BBMDError(rc, "bbmd_batch_set_branches")
+
+    def set_mode(self, mode):
+        """Step path: BATCH_AUTO (persistent when it applies), BATCH_GRAPH or
+        BATCH_PERSISTENT (bbmd_batch_set_mode)."""
+        rc = load().bbmd_batch_set_mode(self.h, int(mode))
+        if rc != BBMD_OK:
+            raise BBMDError(rc, "bbmd_batch_set_mode")
+
+    def uses_persistent(self):
+        return bool(load().bbmd_batch_uses_persistent(self.h))
 
     def step(self, nsteps, dt, thermostats=None):
         """thermostats: None (NVE) or one (kind, T_start, T_end, tau) per replica."""

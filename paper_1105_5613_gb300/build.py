@@ -28,8 +28,8 @@ def _nvcc() -> str:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "bbmd_internal.cuh"),
-            os.path.join(HERE, "..", "include", "bbmd.h")]
+    deps = [src, os.path.join(HERE, "..", "include", "bbmd.h")] + \
+        [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps)
 
 

@@ -1173,9 +1173,19 @@ struct bbmd_batch {
     std::vector<cudaEvent_t> ev;     // fork + joins
     std::string err;
     int device = 0;                  // CUDA device of every replica (current at creation)
+    int mode = BBMD_BATCH_AUTO;      // step path requested (bbmd_batch_set_mode)
+    // persistent step: launch tables, barrier word, grid, staged capacity, generations
+    PersistentStep pst = {};
+    std::vector<void*> pdev;         // device tables of the persistent step
+    int32_t* pctl = nullptr;         // its control words: queue head, finished counts, abort
+    size_t pctl_bytes = 0;           // bytes of head + finished counts (cleared every launch)
+    int pgrid = 0, psmax = 0;
+    std::vector<int> pgen;           // replicas' graph generations at the table upload
 };
 
 namespace {
+
+constexpr int64_t kPersistSteps = 1024;  // steps per launch of the persistent step
 
 bbmd_status batch_fail(bbmd_batch* b, bbmd_status code, const std::string& msg) {
     if (b) b->err = msg;
@@ -1193,6 +1203,27 @@ void batch_free_graphs(bbmd_batch* b) {
 void batch_free_tables(bbmd_batch* b) {
     for (void* p : b->dev) cudaFree(p);
     b->dev.clear();
+}
+
+void batch_free_persistent(bbmd_batch* b) {
+    for (void* p : b->pdev) cudaFree(p);
+    b->pdev.clear();
+    b->pgen.clear();
+    b->pctl = nullptr;
+}
+
+// The persistent step applies when every replica is mixed precision with the block shape
+// of the persistent kernel and the device runs cooperative launches.
+bool persistent_eligible(const bbmd_batch* b) {
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!coop) return false;
+    for (const bbmd_sim* s : b->rep)
+        if (s->d.precision != BBMD_PREC_MIXED || s->d.block_z != kPersistZ) return false;
+    return true;
 }
 
 // Upload systems and CTA offsets for one set of replicas; returns the ManySims view and
@@ -1220,6 +1251,85 @@ bool upload_many(bbmd_batch* b, const std::vector<const DevSim*>& sims,
     m.nrep = (int32_t)nr;
     total = first[nr];
     return true;
+}
+
+
+// Tables of the persistent step for the current replicas: their DevSims, the work items
+// of one step in phase-major order, the items per replica and phase, each phase's
+// predecessor, the control words (queue head and finished counts, then the abort flag),
+// and the grid: every SM's resident CTAs.
+bbmd_status build_persistent(bbmd_batch* b) {
+    cudaStreamSynchronize(b->st);
+    batch_free_persistent(b);
+    const int nr = (int)b->rep.size();
+    // Per-particle and per-cell phases take one item per 2048 particles of a replica (the
+    // device copies of the replicas' DevSims carry that count as grid_part): an item then
+    // outweighs its set-up, and no result of those phases depends on how the particles
+    // are split.  Forces and list builds keep the replica's own CTA counts (the
+    // kinetic-energy partials are summed over grid_cell).
+    std::vector<DevSim> copies((size_t)nr);
+    std::vector<int32_t> need((size_t)nr * kPhases, 0), dep((size_t)nr * kPhases, -1);
+    int smax = 0;
+    for (int r = 0; r < nr; ++r) {
+        DevSim& c = copies[(size_t)r];
+        c = b->rep[(size_t)r]->d;
+        c.grid_part = (int32_t)std::max<int64_t>(1, (c.n + 2047) / 2048);
+        smax = std::max(smax, (int)c.smax);
+        int32_t* nd = &need[(size_t)r * kPhases];
+        for (int ph = 0; ph < kPhases; ++ph) nd[ph] = c.grid_part;
+        nd[kPhScan] = 1;
+        nd[kPhList] = c.nbr_mode == BBMD_NBR_VERLET ? c.grid_list : 0;
+        nd[kPhForce] = c.grid_cell;
+        nd[kPhFinalize] = 1;
+        int last = -1;
+        for (int ph = 0; ph < kPhases; ++ph) {
+            dep[(size_t)r * kPhases + ph] = last;
+            if (nd[ph] > 0) last = ph;
+        }
+    }
+    std::vector<int4> items;
+    for (int ph = 0; ph < kPhases; ++ph)
+        for (int r = 0; r < nr; ++r) {
+            const int c = need[(size_t)r * kPhases + ph];
+            for (int k = 0; k < c; ++k) items.push_back(make_int4(ph, r, k, c));
+        }
+    auto upload = [&](const void* host, size_t bytes) -> void* {
+        void* d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+        b->pdev.push_back(d);
+        if (host && cudaMemcpy(d, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+        return d;
+    };
+    PersistentStep& a = b->pst;
+    a.sims = (const DevSim*)upload(copies.data(), copies.size() * sizeof(DevSim));
+    a.items = (const int4*)upload(items.data(), items.size() * sizeof(int4));
+    a.need = (const int32_t*)upload(need.data(), need.size() * sizeof(int32_t));
+    a.dep = (const int32_t*)upload(dep.data(), dep.size() * sizeof(int32_t));
+    // control words: head, done[nrep][kPhases], abort
+    b->pctl_bytes = (1 + need.size()) * sizeof(int32_t);
+    int32_t* ctl = (int32_t*)upload(nullptr, b->pctl_bytes + sizeof(int32_t));
+    if (!a.sims || !a.items || !a.need || !a.dep || !ctl) {
+        cudaGetLastError();
+        batch_free_persistent(b);
+        return batch_fail(b, BBMD_ERR_OOM, "persistent step tables");
+    }
+    a.head = (uint32_t*)ctl;
+    a.done = ctl + 1;
+    a.abort = ctl + 1 + need.size();
+    a.nrep = nr;
+    a.nitems = (int32_t)items.size();
+    b->pctl = ctl;
+    if (!BBMD_PERSIST_NS::prepare_persistent()) {
+        cudaGetLastError();
+        return batch_fail(b, BBMD_ERR_CUDA, "persistent step shared memory");
+    }
+    const int per_sm = BBMD_PERSIST_NS::persistent_blocks_per_sm(smax);
+    if (per_sm < 1) return batch_fail(b, BBMD_ERR_CUDA, "persistent step does not fit an SM");
+    b->pgrid = per_sm * b->rep[0]->nsm;
+    b->psmax = smax;
+    b->pgen.resize((size_t)nr);
+    for (int r = 0; r < nr; ++r) b->pgen[(size_t)r] = b->rep[(size_t)r]->graph_gen;
+    return BBMD_OK;
 }
 
 // Launches of one step for a group of replicas: one launch per phase for the whole group
@@ -1374,6 +1484,7 @@ void bbmd_destroy_batch(bbmd_batch* b) {
     if (b->st) cudaStreamSynchronize(b->st);
     batch_free_graphs(b);
     batch_free_tables(b);
+    batch_free_persistent(b);
     for (bbmd_sim* s : b->rep) bbmd_destroy(s);
     for (cudaStream_t s : b->side) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
@@ -1405,9 +1516,13 @@ bbmd_status bbmd_create_batch(const bbmd_params* params, int32_t n_rep, const in
         b->own_stream = true;
     }
     bbmd_status rc = BBMD_OK;
+    // the replicas of a batch share one block shape; 0 selects the shape of the persistent
+    // step
+    bbmd_params P = *params;
+    if (P.block_z == 0) P.block_z = kPersistZ;
     for (int32_t r = 0; r < n_rep && rc == BBMD_OK; ++r) {
         bbmd_sim* s = nullptr;
-        rc = bbmd_create(params, n[r], box + 3 * (size_t)r, species[r], pos ? pos[r] : nullptr,
+        rc = bbmd_create(&P, n[r], box + 3 * (size_t)r, species[r], pos ? pos[r] : nullptr,
                          vel ? vel[r] : nullptr, T0[r], seed + (uint64_t)r, b->st, alloc, &s);
         if (rc == BBMD_OK) b->rep.push_back(s);
     }
@@ -1437,6 +1552,42 @@ bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd
         }
     }
     if (nsteps == 0) return BBMD_OK;
+    const bool persistent = b->mode != BBMD_BATCH_GRAPH && persistent_eligible(b);
+    if (b->mode == BBMD_BATCH_PERSISTENT && !persistent)
+        return batch_fail(b, BBMD_ERR_STATE,
+                          "the persistent step needs mixed precision, the batch block shape and "
+                          "cooperative launch");
+    if (persistent) {
+        bool pstale = b->pgen.size() != b->rep.size();
+        for (size_t r = 0; !pstale && r < b->rep.size(); ++r)
+            pstale = b->pgen[r] != b->rep[r]->graph_gen;
+        if (pstale) {
+            bbmd_status rc = build_persistent(b);
+            if (rc != BBMD_OK) return rc;
+        }
+        const bool fshift = b->rep[0]->d.pt.shift == BBMD_SHIFT_FORCE;
+        for (size_t r = 0; r < b->rep.size(); ++r)
+            launch_begin(b->rep[r]->d, b->st, nsteps, dt, nh ? &th[r] : nullptr);
+        // the abort flag is cleared once per call, the queue head and the finished counts
+        // before every launch; a launch runs up to kPersistSteps steps (the queue counts
+        // items of one launch in 32 bits)
+        cudaError_t e0 = cudaMemsetAsync(b->pst.abort, 0, sizeof(int32_t), b->st);
+        if (e0 != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e0));
+        const int64_t per_launch =
+            std::max<int64_t>(1, std::min<int64_t>(kPersistSteps, 0x7fffffff / std::max(1, b->pst.nitems)));
+        for (int64_t k = 0; k < nsteps; k += per_launch) {
+            PersistentStep a = b->pst;
+            a.nsteps = (int32_t)std::min<int64_t>(per_launch, nsteps - k);
+            cudaError_t e = cudaMemsetAsync(b->pctl, 0, b->pctl_bytes, b->st);
+            if (e == cudaSuccess)
+                e = BBMD_PERSIST_NS::launch_persistent_step(a, b->pgrid, b->psmax, nh != 0, fshift, b->st);
+            if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
+        }
+        for (size_t r = 0; r < b->rep.size(); ++r) launch_finish(b->rep[r]->d, b->st);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
+        return BBMD_OK;
+    }
     bool stale = !b->graph[nh] || b->gen[nh].size() != b->rep.size();
     for (size_t r = 0; !stale && r < b->rep.size(); ++r)
         stale = b->gen[nh][r] != b->rep[r]->graph_gen;
@@ -1462,6 +1613,17 @@ bbmd_sim* bbmd_batch_replica(bbmd_batch* b, int32_t r) {
 }
 
 int32_t bbmd_batch_size(const bbmd_batch* b) { return b ? (int32_t)b->rep.size() : 0; }
+
+bbmd_status bbmd_batch_set_mode(bbmd_batch* b, int32_t mode) {
+    if (!b || mode < BBMD_BATCH_AUTO || mode > BBMD_BATCH_PERSISTENT) return BBMD_ERR_ARG;
+    b->mode = mode;
+    return BBMD_OK;
+}
+
+int32_t bbmd_batch_uses_persistent(const bbmd_batch* b) {
+    if (!b) return 0;
+    return b->mode != BBMD_BATCH_GRAPH && persistent_eligible(b) ? 1 : 0;
+}
 
 bbmd_status bbmd_batch_set_branches(bbmd_batch* b, int32_t branches) {
     if (!b || branches < 1) return BBMD_ERR_ARG;

@@ -272,6 +272,40 @@ BBMD_SHAPE_API(z4)
 BBMD_SHAPE_API(z8)
 #undef BBMD_SHAPE_API
 
+// Block shape of the persistent batch step (k_force.cu compiled for it holds the kernel).
+#ifndef BBMD_PERSIST_Z
+#define BBMD_PERSIST_Z 4
+#endif
+constexpr int kPersistZ = BBMD_PERSIST_Z;
+// Persistent batch step (block shape 2 x 2 x kPersistZ, mixed precision): one cooperative launch
+// runs every phase of many steps for every replica.  Work items (phase, replica, CTA
+// index, CTA count) come from one queue, step-major and phase-major within a step; an
+// item starts once its replica's previous non-empty phase has finished.
+enum {
+    kPhIntegrate = 0, kPhCelltop, kPhCheck, kPhZero, kPhBin, kPhScan, kPhScatter, kPhCellsort,
+    kPhGather, kPhCopyback, kPhList, kPhForce, kPhFinalize, kPhases
+};
+struct PersistentStep {
+    const DevSim* sims;       // nrep replica systems (device copies)
+    const int4* items;        // nitems work items {phase, replica, lb, lg}, phase-major
+    const int32_t* need;      // [nrep][kPhases] items per replica and phase
+    const int32_t* dep;       // [nrep][kPhases] the phase an item waits for (-1: none)
+    int32_t* done;            // [nrep][kPhases] finished items, zero at launch
+    uint32_t* head;           // queue head, zero at launch
+    int32_t* abort;           // raised when a wait gives up (stays raised for the call)
+    int32_t nrep, nitems;     // replicas; work items of one step
+    int32_t nsteps;           // steps of this launch (items nitems * nsteps)
+};
+#define BBMD_PERSIST_NS2(n) z##n
+#define BBMD_PERSIST_NS1(n) BBMD_PERSIST_NS2(n)
+#define BBMD_PERSIST_NS BBMD_PERSIST_NS1(BBMD_PERSIST_Z)
+namespace BBMD_PERSIST_NS {
+bool prepare_persistent();                    // kernel attributes (before any capture)
+int persistent_blocks_per_sm(int smax_max);   // resident CTAs per SM
+cudaError_t launch_persistent_step(const PersistentStep& a, int grid, int smax_max, bool ke,
+                                   bool fshift, cudaStream_t st);
+}  // namespace
+
 #define BBMD_SHAPE_DISPATCH(bz, call)          \
     switch (bz) {                              \
         case 1: return z1::call;               \

@@ -497,6 +497,25 @@ struct WarpBox {
     float lo[3], hi[3];
 };
 
+// Shared memory that the force and list bodies use in turn: the staged region's
+// description and its mbarriers, and the per-warp candidate rings.  One instance per
+// kernel, whichever bodies it runs (a kernel running several bodies, such as the
+// persistent batch step, does not pay for each body's own copy).
+struct StageShared {
+    Region R[kStageBuffers];
+    uint64_t mbar[kStageBuffers];
+};
+
+__device__ __forceinline__ StageShared& stage_shared() {
+    __shared__ __align__(16) StageShared ss;
+    return ss;
+}
+
+__device__ __forceinline__ uint32_t* warp_ring(int w) {
+    __shared__ __align__(16) uint32_t ring_all[kBW][kRing];
+    return ring_all[w];
+}
+
 // Bounding box of the active lanes' positions.
 __device__ __forceinline__ WarpBox warp_box(float4 me, bool act) {
     WarpBox b;
@@ -582,8 +601,9 @@ template <int MODE, bool KE, bool FSHIFT>
 __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     if (!force_selected<MODE>(s)) return;  // CTA-uniform, before any barrier
     extern __shared__ float4 smem[];
-    __shared__ Region R[kStageBuffers];
-    __shared__ __align__(8) uint64_t mbar[kStageBuffers];
+    StageShared& ss = stage_shared();
+    Region* const R = ss.R;
+    uint64_t* const mbar = ss.mbar;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0)
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
@@ -600,8 +620,8 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     const float far = kFar;
     const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
     const uint4 sent = make_uint4(sv, sv, sv, sv);
-    __shared__ __align__(16) uint32_t ring_all[MODE == 1 ? kBW : 1][MODE == 1 ? kRing : 4];
-    uint32_t* const ring = ring_all[MODE == 1 ? w : 0];
+    uint32_t* ring = nullptr;  // candidate ring of the stencil mode
+    if constexpr (MODE == 1) ring = warp_ring(w);
     for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar,
                    [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
@@ -836,13 +856,13 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
 __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
     extern __shared__ float4 smem[];
-    __shared__ Region R[kStageBuffers];
-    __shared__ __align__(8) uint64_t mbar[kStageBuffers];
+    StageShared& ss = stage_shared();
+    Region* const R = ss.R;
+    uint64_t* const mbar = ss.mbar;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lcap = s.lcap8 * 8;
     const int lcap2 = lcap >> 1;  // pair slots per particle
-    __shared__ __align__(16) uint32_t ring_all[kBW][kRing];
-    uint32_t* const ring = ring_all[w];
+    uint32_t* const ring = warp_ring(w);
     if (threadIdx.x == 0)
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
     __syncthreads();
@@ -1018,6 +1038,127 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
         }
     });
 }
+
+// ------------------------------------------------------- persistent batch step ----
+// One cooperative launch advances every replica of a batch by many steps.  The step of
+// each replica is a chain of phases (integrate, the two trigger passes, the seven sort
+// passes, the list build, forces, finalize); each phase of each replica is cut into work
+// items with the same (CTA index, CTA count) as the kernels launched for one system, so a
+// replica advances bit for bit as it would alone.  The items of all replicas are handed
+// out from one queue, step after step and phase-major within a step: a CTA takes the next
+// item, waits until the replica's previous non-empty phase is complete (for the first
+// phase of a step: the finalize of the replica's previous step) by a per-replica,
+// per-phase count of finished items (bounded), runs the item and counts it finished.
+// Replicas never wait on each other, so the phases and steps of different replicas
+// overlap; an item waits only on items handed out before it, and every CTA is resident,
+// so the queue always advances.
+#if BBMD_BLOCK_Z == BBMD_PERSIST_Z
+#include "sort_bodies.cuh"
+#include "step_bodies.cuh"
+
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a dependency wait gives up after 1 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Raise the abort flag and ST_TIMEOUT on every replica.
+__device__ __forceinline__ void persistent_abort(const PersistentStep& a) {
+    if (atomicExch(a.abort, 1) == 0)
+        for (int r = 0; r < a.nrep; ++r) atomicOr(&a.sims[r].sc->status, ST_TIMEOUT);
+}
+
+template <bool KE, bool FSHIFT>
+__device__ __forceinline__ void run_phase(int phase, const DevSim& s, int lb, int lg) {
+    switch (phase) {
+        case kPhIntegrate: integrate_body<false>(s, lb, lg); break;
+        case kPhCelltop: celltop_body(s, lb, lg); break;
+        case kPhCheck: check_body(s, lb, lg); break;
+        case kPhZero: zero_body(s, lb, lg); break;
+        case kPhBin: bin_body(s, lb, lg); break;
+        case kPhScan: scan_cta_body(s, lb, lg); break;
+        case kPhScatter: scatter_body(s, lb, lg); break;
+        case kPhCellsort: cellsort_body(s, lb, lg); break;
+        case kPhGather: gather_body(s, lb, lg); break;
+        case kPhCopyback: copyback_body(s, lb, lg); break;
+        case kPhList: list_build_body(s, lb, lg); break;
+        case kPhForce:
+            // the list body, or for a replica whose lists are cut (and in cell mode) the
+            // stencil body: each returns at once when not selected
+            force_body<0, KE, FSHIFT>(s, lb, lg);
+            force_body<1, KE, FSHIFT>(s, lb, lg);
+            break;
+        default: finalize_body(s, KE ? 1 : 0); break;
+    }
+}
+
+template <bool KE, bool FSHIFT>
+__global__ void __launch_bounds__(kBW * 32, 2) k_step_persistent(PersistentStep a) {
+    __shared__ DevSim sh;
+    __shared__ int4 desc;  // phase, replica, lb, lg of the item (phase -1: queue empty)
+    __shared__ int run;    // 0: the item's replica does not rebuild (gated phase)
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int4 d = make_int4(-1, 0, 0, 0);
+            int go = 0;
+            if (*(volatile int*)a.abort == 0) {
+                const long long k = (long long)atomicAdd(a.head, 1u);
+                if (k < (long long)a.nitems * a.nsteps) {
+                    const int step = (int)(k / a.nitems);
+                    d = a.items[k - (long long)step * a.nitems];
+                    int dep = a.dep[d.y * kPhases + d.x], dstep = step;
+                    if (dep < 0 && step > 0) {
+                        dep = kPhFinalize;  // the replica's previous step
+                        dstep = step - 1;
+                    }
+                    if (dep >= 0) {
+                        const int need = a.need[d.y * kPhases + dep] * (dstep + 1);
+                        const int* cnt = &a.done[d.y * kPhases + dep];
+                        const unsigned long long t0 = globaltimer_ns();
+                        while (*(volatile const int*)cnt < need) {
+                            if (*(volatile int*)a.abort) {
+                                d.x = -1;
+                                break;
+                            }
+                            if (globaltimer_ns() - t0 > kWaitNs) {
+                                persistent_abort(a);
+                                d.x = -1;
+                                break;
+                            }
+                        }
+                        __threadfence();
+                    }
+                    go = d.x >= 0;
+                    if (go && d.x >= kPhZero && d.x <= kPhList)
+                        go = *(volatile int*)&a.sims[d.y].sc->rebuild != 0;
+                }
+            }
+            desc = d;
+            run = go;
+        }
+        __syncthreads();
+        const int4 d = desc;
+        if (d.x < 0) return;
+        // data of earlier phases, written by other CTAs, is read by bulk copies (the async
+        // proxy) as well as by ordinary loads
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (run) {
+            const int4* src4 = reinterpret_cast<const int4*>(a.sims + d.y);
+            int4* dst4 = reinterpret_cast<int4*>(&sh);
+            for (int k = threadIdx.x; k < (int)(sizeof(DevSim) / 16); k += blockDim.x) dst4[k] = src4[k];
+            __syncthreads();
+            run_phase<KE, FSHIFT>(d.x, sh, d.z, d.w);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&a.done[d.y * kPhases + d.x], 1);
+        }
+    }
+}
+#endif  // BBMD_BLOCK_Z == BBMD_PERSIST_Z
 
 // ------------------------------------------------------------------ FP64 form ----
 // The same block region staged as exact integer positions in the block's periodic image
@@ -1412,6 +1553,40 @@ void launch_list_build(const DevSim& s, cudaStream_t st) {
     size_t bytes = kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
     k_list_build<<<s.grid_list, kBW * 32, bytes, st>>>(s);
 }
+
+#if BBMD_BLOCK_Z == BBMD_PERSIST_Z
+// Dynamic shared memory of the persistent step for staged capacity smax_max.
+static size_t persistent_smem(int smax_max) {
+    return kStageBuffers * (size_t)(smax_max + 1) * sizeof(float4);
+}
+
+bool prepare_persistent() {
+    g_smem_ok = true;
+    set_smem(k_step_persistent<false, false>);
+    set_smem(k_step_persistent<true, false>);
+    set_smem(k_step_persistent<false, true>);
+    set_smem(k_step_persistent<true, true>);
+    return g_smem_ok;
+}
+
+int persistent_blocks_per_sm(int smax_max) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_persistent<true, false>, kBW * 32,
+                                                  persistent_smem(smax_max));
+    return nb;
+}
+
+cudaError_t launch_persistent_step(const PersistentStep& a, int grid, int smax_max, bool ke,
+                                   bool fshift, cudaStream_t st) {
+    PersistentStep args = a;
+    void* params[] = {&args};
+    const void* fn = ke ? (fshift ? (const void*)k_step_persistent<true, true>
+                                  : (const void*)k_step_persistent<true, false>)
+                        : (fshift ? (const void*)k_step_persistent<false, true>
+                                  : (const void*)k_step_persistent<false, false>);
+    return cudaLaunchCooperativeKernel(fn, grid, kBW * 32, params, persistent_smem(smax_max), st);
+}
+#endif  // BBMD_BLOCK_Z == BBMD_PERSIST_Z
 
 }  // namespace z<BBMD_BLOCK_Z>
 }  // namespace bbmd

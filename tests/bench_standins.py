@@ -101,6 +101,9 @@ class StandinBatch:
     def set_branches(self, branches):
         pass
 
+    def uses_persistent(self):
+        return True
+
     def close(self):
         pass
 

@@ -1,6 +1,7 @@
 """Replica batches (bbmd_create_batch / bbmd_step_batch): every replica of a batch against
-the oracle on its own generated inputs, at its own temperature; one batch graph step per
-step equal, bit for bit, to stepping each replica handle on its own; argument errors."""
+the oracle on its own generated inputs, at its own temperature; the persistent step (one
+cooperative launch per step) and the batch graph both equal, bit for bit, to stepping
+each replica handle on its own; argument errors."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,8 @@ def test_batch_replicas_match_oracle(prec, mode, tol, lcap):
         ns, boxes, pos, vel, sp = lattice_replicas(ms, temps)
     p = bbmd.ka_params(precision=prec, nbr_mode=mode, list_capacity=lcap)
     b = bbmd.Batch(p, ns, boxes, sp, pos, vel)
+    # mixed precision takes the persistent step by default; the FP64 form the graph
+    assert b.uses_persistent() == (prec == 0)
     th = [(bbmd.THERMO_NH, T, T, 0.5) for T in temps]
     b.step(100, 0.005, th)
     for r in range(len(ns)):
@@ -65,20 +68,28 @@ def test_batch_replicas_match_oracle(prec, mode, tol, lcap):
     b.close()
 
 
-@pytest.mark.parametrize("branches", [1, 2, 5])
-def test_batch_step_equals_replica_steps(branches):
+@pytest.mark.parametrize("path,branches,nbr", [("graph", 1, 0), ("graph", 2, 0), ("graph", 5, 0),
+                                              ("persistent", 0, 0), ("persistent", 0, 1)])
+def test_batch_step_equals_replica_steps(path, branches, nbr):
     """RSA replicas of uneven size relaxed by steepest descent, then stepped by the batch
-    graph (replicas grouped into `branches` branches, one launch per phase and group) in
-    one batch and replica by replica in a twin batch: identical states."""
+    (the persistent step, or the graph with replicas grouped into `branches` branches, one
+    launch per phase and group) in one batch and replica by replica in a twin batch:
+    identical states."""
     ns, boxes, pos, sp = gen.replica_batch(5, 2048, 6000, 7)
     temps = list(np.linspace(0.4, 2.0, 5))
-    p = bbmd.ka_params(block_z=2)
+    p = bbmd.ka_params(nbr_mode=nbr)  # the batch default shape: the persistent kernel's
     twins = [bbmd.Batch(p, ns, boxes, sp, pos, None, T0=temps, seed=11) for _ in range(2)]
     for b in twins:
         for r in range(len(ns)):
             b.replica(r).minimize(50)
     th = [(bbmd.THERMO_NH, T, T, 0.5) for T in temps]
-    twins[0].set_branches(branches)
+    if path == "graph":
+        twins[0].set_mode(bbmd.BATCH_GRAPH)
+        twins[0].set_branches(branches)
+        assert not twins[0].uses_persistent()
+    else:
+        twins[0].set_mode(bbmd.BATCH_PERSISTENT)
+        assert twins[0].uses_persistent()
     twins[0].step(60, 0.005, th)
     for r in range(len(ns)):
         twins[1].replica(r).step(60, 0.005, th[r])
@@ -103,6 +114,18 @@ def test_batch_argument_errors():
     assert b.replica(1).observe(0)["step"] == 5
     with pytest.raises(bbmd.BBMDError):
         b.set_branches(0)
+    with pytest.raises(bbmd.BBMDError):
+        b.set_mode(7)
+    b.close()
+    # the persistent step needs mixed precision: asked for with the FP64 form, it is refused
+    b = bbmd.Batch(bbmd.ka_params(precision=bbmd.PREC_FP64), ns, boxes, sp, pos, vel)
+    b.set_mode(bbmd.BATCH_PERSISTENT)
+    assert not b.uses_persistent()
+    with pytest.raises(bbmd.BBMDError) as e:
+        b.step(2, 0.005)
+    assert e.value.code == 8  # BBMD_ERR_STATE
+    b.set_mode(bbmd.BATCH_AUTO)
+    b.step(2, 0.005)
     b.close()
     with pytest.raises(bbmd.BBMDError):  # a replica whose box holds fewer than 3 cells
         bbmd.Batch(bbmd.ka_params(), [4000, 500], [gen.box_for(4000, 1.2), gen.box_for(500, 1.2)],

@@ -137,13 +137,20 @@ enum {
     BBMD_OBS_GR = 8u,        /* partial g_ab(r) (Sec. 4)                                */
     BBMD_OBS_MSD = 16u,      /* mean-square displacement per species since SET_REF      */
     BBMD_OBS_FS = 32u,       /* self-intermediate scattering F_s(k, t) since SET_REF    */
-    BBMD_OBS_SET_REF = 64u   /* store the current unwrapped positions as the reference  */
+    BBMD_OBS_SET_REF = 64u   /* store the current unwrapped positions as the reference
+                                of the time origin args->origin (before MSD / FS)       */
 };
+
+/* Time origins of MSD and F_s: SET_REF stores the unwrapped positions as reference
+ * `origin`, MSD / FS measure against reference `origin` (each origin holds 3n doubles of
+ * device memory once set), so averages over several time origins need no host copies. */
+#define BBMD_MAX_ORIGINS 16
 
 typedef struct {
     int32_t nbins;   /* g(r) bins (0 = 500)  */
     double rmax;     /* g(r) range (0 = 5.0) */
     double k;        /* F_s wave number (0 = 7.25) */
+    int32_t origin;  /* time origin of SET_REF / MSD / FS, in [0, BBMD_MAX_ORIGINS) */
 } bbmd_obs_args;
 
 /* Results of bbmd_observe.  gr_counts[(a*2+b)*nbins + q] counts ordered pairs (i in a,
@@ -223,8 +230,10 @@ bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt,
                                const bbmd_thermostat* thermo, double* ms, int64_t* rebuilds);
 
 /* Measure the observables selected by mask at the current state (synchronising).  args may
- * be NULL for the defaults.  out->gr_counts / out->gr are filled when non-NULL and GR is
- * set. */
+ * be NULL for the defaults (time origin 0).  out->gr_counts / out->gr are filled when
+ * non-NULL and GR is set.  MSD / FS of an origin never set by SET_REF -> BBMD_ERR_STATE.
+ * ENERGY / VIRIAL evaluate pair energies in FP64 from the exact integer positions in
+ * mixed precision too (the forces of the step stay the FP32 kernel's). */
 bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args,
                          bbmd_obs* out);
 

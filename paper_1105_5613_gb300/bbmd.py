@@ -27,6 +27,7 @@ NBR_VERLET, NBR_CELL = 0, 1
 THERMO_NVE, THERMO_NH = 0, 1
 OBS_ENERGY, OBS_VIRIAL, OBS_MOMENTUM, OBS_GR, OBS_MSD, OBS_FS, OBS_SET_REF = 1, 2, 4, 8, 16, 32, 64
 BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
+MAX_ORIGINS = 16
 
 
 class BBMDError(RuntimeError):
@@ -60,7 +61,8 @@ class bbmd_alloc(C.Structure):
 
 
 class bbmd_obs_args(C.Structure):
-    _fields_ = [("nbins", C.c_int32), ("rmax", C.c_double), ("k", C.c_double)]
+    _fields_ = [("nbins", C.c_int32), ("rmax", C.c_double), ("k", C.c_double),
+                ("origin", C.c_int32)]
 
 
 class bbmd_obs(C.Structure):
@@ -306,7 +308,7 @@ class Sim:
                                                  _dp(ms), C.byref(nreb)))
         return dict(zip(PHASES, ms.tolist())), int(nreb.value)
 
-    def observe(self, mask, nbins=500, rmax=5.0, k=7.25):
+    def observe(self, mask, nbins=500, rmax=5.0, k=7.25, origin=0):
         o = bbmd_obs()
         counts = g = None
         if mask & OBS_GR:
@@ -314,7 +316,7 @@ class Sim:
             g = np.zeros((2, 2, nbins))
             o.gr_counts = counts.ctypes.data_as(C.POINTER(C.c_uint64))
             o.gr = _dp(g)
-        args = bbmd_obs_args(nbins, rmax, k)
+        args = bbmd_obs_args(nbins, rmax, k, origin)
         _check(self.h, load().bbmd_observe(self.h, mask, C.byref(args), C.byref(o)))
         res = {f: getattr(o, f) for f in ("ke", "pe", "virial", "pressure", "temperature", "xi",
                                           "eta", "conserved", "step", "n_rebuilds")}

@@ -29,7 +29,7 @@ struct bbmd_sim {
     int64_t gr_scratch_n = 0;
     unsigned long long* gr_counts = nullptr;
     int gr_nbins = 0;
-    bool ref_set = false;
+    double* ref[BBMD_MAX_ORIGINS] = {};  // unwrapped positions by id of each time origin
     int sticky = 0;
     int device = 0;                  // CUDA device of the handle (current at creation)
     int nsm = 1;
@@ -769,18 +769,19 @@ bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args
         launch_force(D, sim->st, true, false);
         launch_reduce_partials(D, sim->st, -3, sim->dout + 8);
     }
+    const int origin = args ? args->origin : 0;
+    if (origin < 0 || origin >= BBMD_MAX_ORIGINS)
+        return fail(sim, BBMD_ERR_ARG, "origin must be in [0, BBMD_MAX_ORIGINS)");
     if (mask & BBMD_OBS_SET_REF) {
-        if (!D.ref) {
-            D.ref = (double*)dev_alloc(sim, 3 * D.n * 8);
-            if (!D.ref) return fail(sim, BBMD_ERR_OOM, "reference positions");
-            free_graphs(sim);  // the captured kernels hold the old DevSim copy
+        if (!sim->ref[origin]) {
+            sim->ref[origin] = (double*)dev_alloc(sim, 3 * D.n * 8);
+            if (!sim->ref[origin]) return fail(sim, BBMD_ERR_OOM, "reference positions");
         }
-        launch_set_ref(D, sim->st);
-        sim->ref_set = true;
+        launch_set_ref(D, sim->st, sim->ref[origin]);
     }
     if (mask & (BBMD_OBS_MSD | BBMD_OBS_FS)) {
-        if (!sim->ref_set) return fail(sim, BBMD_ERR_STATE, "MSD/FS need SET_REF first");
-        launch_msd_fs(D, sim->st, kv, sim->dout + 16);
+        if (!sim->ref[origin]) return fail(sim, BBMD_ERR_STATE, "MSD/FS need SET_REF of this origin first");
+        launch_msd_fs(D, sim->st, sim->ref[origin], kv, sim->dout + 16);
     }
     std::vector<unsigned long long> counts;
     if (mask & BBMD_OBS_GR) {

@@ -102,7 +102,6 @@ struct alignas(16) DevSim {
     uint16_t* list;
     uint16_t* cellmax;       // per cell: list length in units of 8 entries
     double* partials;        // [kMaxPartials][4]
-    double* ref;             // [3][n] unwrapped reference positions by id (SET_REF)
     DevScalars* sc;
     int32_t grid_part;       // grid of per-particle grid-stride kernels
     int32_t grid_cell;       // grid of the force kernel (kBlockWarps warps per CTA)
@@ -349,8 +348,10 @@ void launch_init_fcc(const DevSim& s, cudaStream_t st, int m, double jitter, uin
 void launch_init_mb(const DevSim& s, cudaStream_t st, double T0, uint64_t seed, double* tmp3);
 void launch_sd_step(const DevSim& s, cudaStream_t st, double hmax, double dmax);
 void launch_clear_rebuild(const DevSim& s, cudaStream_t st);
-void launch_set_ref(const DevSim& s, cudaStream_t st);
-void launch_msd_fs(const DevSim& s, cudaStream_t st, double kvec, double* out_dev);
+// unwrapped positions by id (3 x n doubles) into ref / MSD and F_s against ref
+void launch_set_ref(const DevSim& s, cudaStream_t st, double* ref);
+void launch_msd_fs(const DevSim& s, cudaStream_t st, const double* ref, double kvec,
+                   double* out_dev);
 int launch_gr(const DevSim& s, cudaStream_t st, int nbins, double rmax,
               unsigned long long* counts_dev, int32_t* scratch_i32, float4* scratch_f4,
               int64_t scratch_n);

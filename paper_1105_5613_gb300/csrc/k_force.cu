@@ -504,7 +504,20 @@ struct WarpBox {
 struct StageShared {
     Region R[kStageBuffers];
     uint64_t mbar[kStageBuffers];
+    // the block's cells are handed to the warps in turn as they come free (a count per
+    // block parity: one in use, the other reset for the next block)
+    int next_cell[2];
+    // kinetic energy of each cell of the block (sums of its chunks), summed in cell order
+    // once the block is done: the same total whichever warp took which cell
+    double cell_ke[2][kCells];
 };
+
+// The next cell of the block for this warp (kCells when none is left).
+__device__ __forceinline__ int take_cell(StageShared& ss, int par, int lane) {
+    int cw = 0;
+    if (lane == 0) cw = atomicAdd(&ss.next_cell[par], 1);
+    return __shfl_sync(0xffffffffu, cw, 0);
+}
 
 __device__ __forceinline__ StageShared& stage_shared() {
     __shared__ __align__(16) StageShared ss;
@@ -605,12 +618,15 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     Region* const R = ss.R;
     uint64_t* const mbar = ss.mbar;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
+        ss.next_cell[0] = ss.next_cell[1] = 0;
+        for (int q = 0; q < 2; ++q)
+            for (int c = 0; c < kCells; ++c) ss.cell_ke[q][c] = 0.0;
+    }
     __syncthreads();
-    // per-lane kinetic energy in compensated FP32 (sum + carried rounding error), reduced in
-    // FP64 at the end; no FP64 instruction runs per chunk
-    float ke_sum = 0.f, ke_err = 0.f;
+    double ke_cta = 0.0;  // thread 0: kinetic energy of the finished blocks, in order
+    int blk_it = 0;       // blocks of this CTA so far (the parity selects the counters)
     float hdt0 = 0.f, hdt1 = 0.f;
     if (KE) {
         hdt0 = s.sc->hdt[0];
@@ -625,13 +641,25 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar,
                    [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
-        for (int cw = w; cw < kCells; cw += kBW) {
+        const int par = blk_it & 1;
+        if (threadIdx.x == 0) {
+            // the other parity's counters: the previous block is done (its kinetic energy
+            // is added to the CTA's in cell order) and the next block starts from zero
+            ss.next_cell[par ^ 1] = 0;
+            if (KE && blk_it > 0)
+                for (int c = 0; c < kCells; ++c) {
+                    ke_cta += ss.cell_ke[par ^ 1][c];
+                    ss.cell_ke[par ^ 1][c] = 0.0;
+                }
+        }
+        ++blk_it;
+        for (int cw = take_cell(ss, par, lane); cw < kCells; cw = take_cell(ss, par, lane)) {
             const WarpCell wc = warp_cell(s, bp, cw);
             const int i0 = wc.valid ? Rc.start[wc.rq] : 0;
             const int cnt = wc.valid ? staged_count(Rc, wc.rq) : 0;
             const int self0 = Rc.off[wc.rq];
-            // the warp's next cell: its first list rows, velocities and row count go to L2
-            // now, so that its prologue does not wait on DRAM
+            // a cell a warp will take next: its first list rows, velocities and row count
+            // go to L2 now, so that its prologue does not wait on DRAM
             if (MODE == 0 && cw + kBW < kCells) {
                 const WarpCell wn = warp_cell(s, bp, cw + kBW);
                 if (wn.valid) {
@@ -816,29 +844,34 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                     if (!(isfinite(fx) && isfinite(fy) && isfinite(fz))) set_status(s, ST_NONFINITE);
                     s.F[gi] = make_float4(fx, fy, fz, 0.f);
                 }
-                if (KE && act) {
-                    if (MODE == 1) {
-                        v0 = s.v[gi];
-                        v1 = s.v[s.npad + gi];
-                        v2 = s.v[2 * s.npad + gi];
+                if (KE) {
+                    float k = 0.f;
+                    if (act) {
+                        if (MODE == 1) {
+                            v0 = s.v[gi];
+                            v1 = s.v[s.npad + gi];
+                            v2 = s.v[2 * s.npad + gi];
+                        }
+                        const float h = si ? hdt1 : hdt0;
+                        const float m = si ? m1 : m0;
+                        const float vx = fmaf(h, fx, i64_to_f32_fast(v0) * pow2f(-kVelExp));
+                        const float vy = fmaf(h, fy, i64_to_f32_fast(v1) * pow2f(-kVelExp));
+                        const float vz = fmaf(h, fz, i64_to_f32_fast(v2) * pow2f(-kVelExp));
+                        k = 0.5f * m * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
                     }
-                    const float h = si ? hdt1 : hdt0;
-                    const float m = si ? m1 : m0;
-                    const float vx = fmaf(h, fx, i64_to_f32_fast(v0) * pow2f(-kVelExp));
-                    const float vy = fmaf(h, fy, i64_to_f32_fast(v1) * pow2f(-kVelExp));
-                    const float vz = fmaf(h, fz, i64_to_f32_fast(v2) * pow2f(-kVelExp));
-                    const float k = 0.5f * m * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-                    // Kahan step: ke_err carries the low part lost by the previous additions
-                    const float y = k - ke_err;
-                    const float t = ke_sum + y;
-                    ke_err = (t - ke_sum) - y;
-                    ke_sum = t;
+                    // the chunk's sum in FP64, added to its cell's (chunks of a cell run in
+                    // order on one warp)
+                    const double kc = warp_sum_d((double)k);
+                    if (lane == 0) ss.cell_ke[par][cw] += kc;
                 }
             }
         }
     });
     if (KE) {
-        const double acc_ke = warp_sum_d((double)ke_sum - (double)ke_err);
+        // the last block's cells (every warp has passed the block's closing barrier)
+        if (threadIdx.x == 0 && blk_it > 0)
+            for (int c = 0; c < kCells; ++c) ke_cta += ss.cell_ke[(blk_it - 1) & 1][c];
+        const double acc_ke = threadIdx.x == 0 ? ke_cta : 0.0;
         block_partials(s, lb, &acc_ke, 0, 1);
     }
 }
@@ -863,16 +896,22 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
     const int lcap = s.lcap8 * 8;
     const int lcap2 = lcap >> 1;  // pair slots per particle
     uint32_t* const ring = warp_ring(w);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
+        ss.next_cell[0] = ss.next_cell[1] = 0;
+    }
     __syncthreads();
+    int blk_it = 0;  // blocks of this CTA so far (the parity selects the cell counter)
     const float far = kFar;
     const unsigned sentpair = (unsigned)s.smax | ((unsigned)s.smax << 16);
     uint32_t* list32 = reinterpret_cast<uint32_t*>(s.list);
     const int64_t rowstep = (int64_t)s.npad * 4;  // uint32 distance between kb rows
     for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar, [&](const BlockPos& bp, const Region& Rc,
                                                            const float4* sm) {
-        for (int cw = w; cw < kCells; cw += kBW) {
+        const int par = blk_it & 1;
+        if (threadIdx.x == 0) ss.next_cell[par ^ 1] = 0;  // for the next block
+        ++blk_it;
+        for (int cw = take_cell(ss, par, lane); cw < kCells; cw = take_cell(ss, par, lane)) {
             const WarpCell wc = warp_cell(s, bp, cw);
             const int i0 = wc.valid ? Rc.start[wc.rq] : 0;
             const int cnt = wc.valid ? staged_count(Rc, wc.rq) : 0;

@@ -534,21 +534,22 @@ __global__ void __launch_bounds__(kThreads) k_list_ids(DevSim s, const int32_t* 
 
 // ------------------------------------------------------------ MSD and F_s ----
 
-__global__ void __launch_bounds__(kThreads) k_set_ref(DevSim s, double Lx, double Ly, double Lz) {
+__global__ void __launch_bounds__(kThreads) k_set_ref(DevSim s, double* ref, double Lx, double Ly,
+                                                     double Lz) {
     const double L[3] = {Lx, Ly, Lz};
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
          k += (int64_t)gridDim.x * blockDim.x) {
         int64_t id = s.id[k];
         for (int d = 0; d < 3; ++d) {
             int64_t idx = d * s.npad + k;
-            s.ref[d * s.n + id] =
+            ref[d * s.n + id] =
                 ldexp(__ll2double_rn((long long)s.x[idx]), -s.kexp) + L[d] * (double)s.img[idx];
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_msd_fs(DevSim s, double kv, double Lx, double Ly,
-                                                    double Lz) {
+__global__ void __launch_bounds__(kThreads) k_msd_fs(DevSim s, const double* ref, double kv,
+                                                    double Lx, double Ly, double Lz) {
     const double L[3] = {Lx, Ly, Lz};
     double acc[6] = {0, 0, 0, 0, 0, 0};  // msdA, msdB, fsA, fsB, nA, nB
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;
@@ -559,7 +560,7 @@ __global__ void __launch_bounds__(kThreads) k_msd_fs(DevSim s, double kv, double
         for (int d = 0; d < 3; ++d) {
             int64_t idx = d * s.npad + k;
             double u = ldexp(__ll2double_rn((long long)s.x[idx]), -s.kexp) + L[d] * (double)s.img[idx];
-            double du = u - s.ref[d * s.n + id];
+            double du = u - ref[d * s.n + id];
             d2 += du * du;
             c += cos(kv * du);
         }
@@ -667,14 +668,15 @@ void launch_sd_step(const DevSim& s, cudaStream_t st, double hmax, double dmax) 
 
 void launch_clear_rebuild(const DevSim& s, cudaStream_t st) { k_clear_rebuild<<<1, 1, 0, st>>>(s); }
 
-void launch_set_ref(const DevSim& s, cudaStream_t st) {
-    k_set_ref<<<s.grid_part, kThreads, 0, st>>>(s, ldexp((double)s.Lfix[0], -s.kexp),
+void launch_set_ref(const DevSim& s, cudaStream_t st, double* ref) {
+    k_set_ref<<<s.grid_part, kThreads, 0, st>>>(s, ref, ldexp((double)s.Lfix[0], -s.kexp),
                                                 ldexp((double)s.Lfix[1], -s.kexp),
                                                 ldexp((double)s.Lfix[2], -s.kexp));
 }
 
-void launch_msd_fs(const DevSim& s, cudaStream_t st, double kvec, double* out_dev) {
-    k_msd_fs<<<s.grid_part, kThreads, 0, st>>>(s, kvec, ldexp((double)s.Lfix[0], -s.kexp),
+void launch_msd_fs(const DevSim& s, cudaStream_t st, const double* ref, double kvec,
+                   double* out_dev) {
+    k_msd_fs<<<s.grid_part, kThreads, 0, st>>>(s, ref, kvec, ldexp((double)s.Lfix[0], -s.kexp),
                                                ldexp((double)s.Lfix[1], -s.kexp),
                                                ldexp((double)s.Lfix[2], -s.kexp));
     k_reduce_partials<<<1, 256, 0, st>>>(s, s.grid_part, 6, out_dev, 0);

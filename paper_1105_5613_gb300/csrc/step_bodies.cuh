@@ -142,21 +142,22 @@ __device__ __forceinline__ void integrate_body(const DevSim& s, int lb, int lg) 
 //   (1) Verlet mode: a pair of the same or of neighbouring build cells that the list left
 //       out.  Its distance at the build was at least rc_ab + skin, so it interacts only
 //       after closing more than the skin.
-//   (2) Both modes: a pair whose build cells are two or more apart along some axis.  One
-//       whole cell of side D lies between them, so they were more than D_min apart (the
-//       smallest side over the axes) and interact only after closing more than
-//       D_min - rc_max, where rc_max is the largest cutoff.  The cell grid makes
-//       D_min >= rc_max + skin, but by little when the cells just fit.
+//   (2) Both modes: a pair whose build cells are two apart along some axis (and at most
+//       two apart along every axis: pairs three or more cells apart would have to close
+//       more than 2 D - rc).  One whole cell of side D lies between them, so they were
+//       more than D_min apart (the smallest side over the axes) and interact only after
+//       closing more than D_min - rc_max, where rc_max is the largest cutoff.  The cell
+//       grid makes D_min >= rc_max + skin, but by little when the cells just fit.
 // Rule (1) compares, for every build cell, its two largest displacements, and its largest
-// with the largest of each of its 26 neighbours, with the skin.  Rule (2) compares the two
-// largest displacements of the whole system with D_min - rc_max.  Both thresholds carry a
-// relative margin of 1e-4 against the FP32 rounding of the displacements.  Cell mode
-// evaluates every pair of the 27 build cells at every step, so only rule (2) applies there.
-// Pass 1 finds the two largest displacements of every cell (a warp per cell, the particles
-// of a cell being contiguous) and of every CTA's cells (partials 6 and 7); pass 2 applies
-// rule (1) from the cells whose largest displacement exceeds half the skin, and its CTA 0
-// merges the CTA pairs of pass 1 for rule (2).  Both passes run only in steps where some
-// displacement exceeds half of the smaller threshold.
+// with the largest of each of its 26 neighbours, with the skin.  Rule (2) compares its
+// largest with the largest of each cell of the 5 x 5 x 5 block around it (and with its own
+// second largest) with D_min - rc_max.  Both thresholds carry a relative margin of 1e-4
+// against the FP32 rounding of the displacements.  Cell mode evaluates every pair of the
+// 27 build cells at every step, so only rule (2) applies there.  Pass 1 finds the two
+// largest displacements of every cell (a warp per cell, the particles of a cell being
+// contiguous); pass 2 applies the rules from the cells whose largest displacement exceeds
+// half of the smaller threshold.  Both passes run only in steps where some displacement
+// exceeds that half.
 __device__ __forceinline__ void top2_insert(float v, float& a, float& b) {
     if (v > a) {
         b = a;
@@ -166,87 +167,59 @@ __device__ __forceinline__ void top2_insert(float v, float& a, float& b) {
     }
 }
 
-__device__ __forceinline__ void warp_top2(float& a, float& b) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float oa = __shfl_xor_sync(kStepFull, a, o);
-        const float ob = __shfl_xor_sync(kStepFull, b, o);
-        top2_insert(oa, a, b);
-        top2_insert(ob, a, b);
-    }
-}
-
-constexpr int kTopQ = 6;  // partials 6 and 7: the two largest displacements of each CTA
-
 __device__ __forceinline__ void celltop_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->near) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)lg * (blockDim.x >> 5);
-    float wa = 0.f, wb = 0.f;  // the warp's two largest over its cells
     for (int64_t c = (lb * (int64_t)blockDim.x + threadIdx.x) >> 5; c < s.ncell; c += nwarps) {
         const int st = s.cell_start[c], en = s.cell_start[c + 1];
         float a = 0.f, b = 0.f;
         for (int k = st + lane; k < en; k += 32) top2_insert(s.disp[k], a, b);
-        warp_top2(a, b);
-        if (lane == 0) s.mtop[c] = make_float2(a, b);
-        top2_insert(a, wa, wb);
-        top2_insert(b, wa, wb);
-    }
-    __shared__ float2 red[kStepThreads / 32];
-    if (lane == 0) red[w] = make_float2(wa, wb);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float a = 0.f, b = 0.f;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            top2_insert(red[k].x, a, b);
-            top2_insert(red[k].y, a, b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oa = __shfl_xor_sync(kStepFull, a, o);
+            const float ob = __shfl_xor_sync(kStepFull, b, o);
+            top2_insert(oa, a, b);
+            top2_insert(ob, a, b);
         }
-        s.partials[kTopQ * kMaxPartials + lb] = a;
-        s.partials[(kTopQ + 1) * kMaxPartials + lb] = b;
+        if (lane == 0) s.mtop[c] = make_float2(a, b);
     }
 }
 
-// Pass 1 ran on grid_part CTAs (of the system, or of its replica in a batch launch).
+// Periodic cell index for a in [-2, n + 2) (every axis has at least 3 cells).
+__device__ __forceinline__ int wrap_cell(int a, int n) {
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
 __device__ __forceinline__ void check_body(const DevSim& s, int lb, int lg) {
     DevScalars* sc = s.sc;
     if (!sc->near) return;
+    const bool verlet = s.nbr_mode == BBMD_NBR_VERLET;
+    const float thr1 = s.disp_thr, thr2 = s.disp_far;
+    const float start = 0.5f * (verlet ? fminf(thr1, thr2) : thr2);
     bool need = false;
-    if (lb == 0 && threadIdx.x < 32) {
-        // rule (2): the two largest displacements of the system
-        float a = 0.f, b = 0.f;
-        for (int k = threadIdx.x; k < s.grid_part; k += 32) {
-            top2_insert((float)s.partials[kTopQ * kMaxPartials + k], a, b);
-            top2_insert((float)s.partials[(kTopQ + 1) * kMaxPartials + k], a, b);
-        }
-        warp_top2(a, b);
-        if (a + b > s.disp_far) need = true;
-    }
-    if (s.nbr_mode == BBMD_NBR_VERLET) {
-        // rule (1)
-        const float thr = s.disp_thr;
-        for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < s.ncell;
-             c += (int64_t)lg * blockDim.x) {
-            const float2 m = s.mtop[c];
-            if (m.x <= 0.5f * thr) continue;
-            float mx = m.y;  // the cell's own second largest
-            int a[3];
-            cell_coords((int)c, s.nc, a[0], a[1], a[2]);
-            for (int dz = -1; dz <= 1; ++dz) {
-                int z = a[2] + dz;
-                z = z < 0 ? z + s.nc[2] : (z >= s.nc[2] ? z - s.nc[2] : z);
-                for (int dy = -1; dy <= 1; ++dy) {
-                    int y = a[1] + dy;
-                    y = y < 0 ? y + s.nc[1] : (y >= s.nc[1] ? y - s.nc[1] : y);
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if ((dx | dy | dz) == 0) continue;
-                        int x = a[0] + dx;
-                        x = x < 0 ? x + s.nc[0] : (x >= s.nc[0] ? x - s.nc[0] : x);
-                        mx = fmaxf(mx, s.mtop[(z * s.nc[1] + y) * s.nc[0] + x].x);
-                    }
+    for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < s.ncell;
+         c += (int64_t)lg * blockDim.x) {
+        const float2 m = s.mtop[c];
+        if (m.x <= start) continue;
+        float m27 = m.y, m125 = m.y;  // the cell's own second largest
+        int a[3];
+        cell_coords((int)c, s.nc, a[0], a[1], a[2]);
+        for (int dz = -2; dz <= 2; ++dz) {
+            const int z = wrap_cell(a[2] + dz, s.nc[2]);
+            for (int dy = -2; dy <= 2; ++dy) {
+                const int y = wrap_cell(a[1] + dy, s.nc[1]);
+                for (int dx = -2; dx <= 2; ++dx) {
+                    if ((dx | dy | dz) == 0) continue;
+                    const int x = wrap_cell(a[0] + dx, s.nc[0]);
+                    const float v = s.mtop[(z * s.nc[1] + y) * s.nc[0] + x].x;
+                    m125 = fmaxf(m125, v);
+                    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
+                        m27 = fmaxf(m27, v);
                 }
             }
-            if (m.x + mx > thr) need = true;
         }
+        if ((verlet && m.x + m27 > thr1) || m.x + m125 > thr2) need = true;
     }
     if (need) sc->rebuild = 1;
 }

@@ -46,3 +46,16 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "bbmd_oracle" not in txt, f
+
+
+def test_observe_args_layout_and_origin_count_match_header():
+    import os
+    import re
+
+    from paper_1105_5613_gb300 import bbmd
+
+    # int32 (+4 padding), 2 doubles, int32 (+4 padding)
+    assert ctypes.sizeof(bbmd.bbmd_obs_args) == 32
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "bbmd.h")).read()
+    assert int(re.search(r"#define BBMD_MAX_ORIGINS (\d+)", hdr).group(1)) == bbmd.MAX_ORIGINS
+    assert int(re.search(r"BBMD_BATCH_PERSISTENT = (\d+)", hdr).group(1)) == bbmd.BATCH_PERSISTENT

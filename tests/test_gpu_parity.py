@@ -295,6 +295,35 @@ def test_msd_fs_after_200_steps(prec, tol):
     sim.close()
 
 
+def test_msd_fs_several_time_origins():
+    """Three time origins set 40 steps apart, each measured at the end against the oracle's
+    positions and image counters at that origin (FP64 form: the trajectories agree to
+    1e-9); an origin never set is refused."""
+    sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.05, T=2.0, precision=bbmd.PREC_FP64)
+    xq, _, _ = quantized(pos, L)
+    st = oracle.MDState(xq, vel, sp, L, oracle_params(p))
+    th = (1.5, 1.5, 0.5)
+    refs = []
+    for o in range(3):
+        sim.observe(bbmd.OBS_SET_REF, origin=o)
+        refs.append((st.pos.copy(), st.image.copy()))
+        sim.step(40, 0.005, (bbmd.THERMO_NH, *th))
+        oracle.md_run(st, 40, 0.005, thermo=th, use_cells=True)
+    got = [sim.observe(bbmd.OBS_MSD | bbmd.OBS_FS, origin=o) for o in range(3)]
+    for o in range(3):
+        msd, fs = oracle.msd_fs(st.pos, st.image, refs[o][0], refs[o][1], sp, L, 7.25)
+        assert np.allclose(got[o]["msd"], msd, rtol=1e-7), (o, got[o]["msd"], msd)
+        assert np.allclose(got[o]["fs"], fs, rtol=0, atol=1e-7), (o, got[o]["fs"], fs)
+    assert got[0]["msd"][0] > got[1]["msd"][0] > got[2]["msd"][0] > 0  # longer lag, farther
+    with pytest.raises(bbmd.BBMDError) as e:
+        sim.observe(bbmd.OBS_MSD, origin=5)
+    assert e.value.code == 8  # BBMD_ERR_STATE
+    with pytest.raises(bbmd.BBMDError) as e:
+        sim.observe(bbmd.OBS_MSD, origin=bbmd.MAX_ORIGINS)
+    assert e.value.code == 1
+    sim.close()
+
+
 def test_msd_fs_rigid_translation():
     sim, n, L, pos, vel, sp, p = make(ncell=8, shake=0.1)
     sim.observe(bbmd.OBS_SET_REF)

@@ -601,7 +601,7 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     D.cell_start = (int32_t*)A((ncell + 1) * 4);
     D.scan_part = (int32_t*)A(((ncell + 8191) / 8192 + 1) * 4);
     if (params->nbr_mode == BBMD_NBR_VERLET) D.list = (uint16_t*)A((size_t)D.lcap8 * np * 16);
-    D.cellmax = (uint16_t*)A(np * 2);
+    D.rows = (uint16_t*)A(np * 2);
     D.partials = (double*)A((size_t)8 * kMaxPartials * 8);
     D.disp = (float*)A(np * 4);
     D.mtop = (float2*)A((size_t)ncell * 8);
@@ -612,7 +612,7 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
         return BBMD_ERR_OOM;
     }
     if (cudaMemsetAsync(D.sc, 0, sizeof(DevScalars), sim->st) != cudaSuccess ||
-        cudaMemsetAsync(D.cellmax, 0, np * 2, sim->st) != cudaSuccess ||
+        cudaMemsetAsync(D.rows, 0, np * 2, sim->st) != cudaSuccess ||
         cudaMemsetAsync(D.img, 0, 3 * np * 4, sim->st) != cudaSuccess ||
         cudaMemsetAsync(D.disp, 0, np * 4, sim->st) != cudaSuccess) {
         bbmd_destroy(sim);

@@ -100,7 +100,7 @@ struct alignas(16) DevSim {
     double* ud;              // per-particle FP64 energy (energy passes)
     int32_t *key, *cell_start, *count, *cursor, *perm, *perm_tmp, *scan_part;
     uint16_t* list;
-    uint16_t* cellmax;       // per cell: list length in units of 8 entries
+    uint16_t* rows;          // per particle: rows (8 entries each) of its Verlet list
     double* partials;        // [kMaxPartials][4]
     DevScalars* sc;
     int32_t grid_part;       // grid of per-particle grid-stride kernels

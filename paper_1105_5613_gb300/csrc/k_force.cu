@@ -504,15 +504,44 @@ struct WarpBox {
 struct StageShared {
     Region R[kStageBuffers];
     uint64_t mbar[kStageBuffers];
-    // the block's cells are handed to the warps in turn as they come free (a count per
-    // block parity: one in use, the other reset for the next block)
+    // the block's work items (cells, or chunks of 32 particles) are handed to the warps in
+    // turn as they come free (a count per block parity: one in use, the other reset for
+    // the next block)
     int next_cell[2];
-    // kinetic energy of each cell of the block (sums of its chunks), summed in cell order
-    // once the block is done: the same total whichever warp took which cell
-    double cell_ke[2][kCells];
+    // list-mode chunks of the block: the own particles, species A first then B (each cell
+    // holds its A particles first), 32 to a chunk across the block's cells.  Per own cell
+    // (in cell order): staged offset, first particle, count, A count; prefixes of the A
+    // and B counts; the number of A chunks and of all chunks.
+    int c_off[kCells], c_i0[kCells], c_n[kCells], c_nA[kCells];
+    int prefA[kCells + 1], prefB[kCells + 1];
+    int nchA, nch;
+    // kinetic energy of the CTA's chunks in 2^-32 fixed point: integer sums do not depend
+    // on which warp added which chunk when
+    unsigned long long ke_fix;
 };
 
-// The next cell of the block for this warp (kCells when none is left).
+// Lane `lane` of list-mode chunk `item` of the block: the particle's ordinal o among the
+// block's particles of the chunk's species, its cell q (the last whose prefix is <= o: a
+// cell with particles), its global index gi and staged index self.
+__device__ __forceinline__ void chunk_lane(const StageShared& ss, int item, int lane, bool& act,
+                                           int64_t& gi, int& self) {
+    const bool isB = item >= ss.nchA;
+    const int o = (isB ? item - ss.nchA : item) * 32 + lane;
+    const int* pref = isB ? ss.prefB : ss.prefA;
+    act = o < pref[kCells];
+    int q = 0, hi = kCells - 1;
+    while (q < hi) {
+        const int mid = (q + hi + 1) >> 1;
+        if (pref[mid] <= o) q = mid;
+        else hi = mid - 1;
+    }
+    const int li = (isB ? ss.c_nA[q] : 0) + (o - pref[q]);
+    gi = act ? (int64_t)ss.c_i0[q] + li : 0;
+    self = act ? ss.c_off[q] + li : 0;
+}
+
+// The next work item of the block for this warp (at least the item count when none is
+// left).
 __device__ __forceinline__ int take_cell(StageShared& ss, int par, int lane) {
     int cw = 0;
     if (lane == 0) cw = atomicAdd(&ss.next_cell[par], 1);
@@ -621,12 +650,10 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
         ss.next_cell[0] = ss.next_cell[1] = 0;
-        for (int q = 0; q < 2; ++q)
-            for (int c = 0; c < kCells; ++c) ss.cell_ke[q][c] = 0.0;
+        ss.ke_fix = 0ull;
     }
     __syncthreads();
-    double ke_cta = 0.0;  // thread 0: kinetic energy of the finished blocks, in order
-    int blk_it = 0;       // blocks of this CTA so far (the parity selects the counters)
+    int blk_it = 0;  // blocks of this CTA so far (the parity selects the counter)
     float hdt0 = 0.f, hdt1 = 0.f;
     if (KE) {
         hdt0 = s.sc->hdt[0];
@@ -642,53 +669,96 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                    [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
         const int par = blk_it & 1;
-        if (threadIdx.x == 0) {
-            // the other parity's counters: the previous block is done (its kinetic energy
-            // is added to the CTA's in cell order) and the next block starts from zero
-            ss.next_cell[par ^ 1] = 0;
-            if (KE && blk_it > 0)
-                for (int c = 0; c < kCells; ++c) {
-                    ke_cta += ss.cell_ke[par ^ 1][c];
-                    ss.cell_ke[par ^ 1][c] = 0.0;
-                }
-        }
+        if (threadIdx.x == 0) ss.next_cell[par ^ 1] = 0;  // for the next block
         ++blk_it;
-        for (int cw = take_cell(ss, par, lane); cw < kCells; cw = take_cell(ss, par, lane)) {
-            const WarpCell wc = warp_cell(s, bp, cw);
-            const int i0 = wc.valid ? Rc.start[wc.rq] : 0;
-            const int cnt = wc.valid ? staged_count(Rc, wc.rq) : 0;
-            const int self0 = Rc.off[wc.rq];
-            // a cell a warp will take next: its first list rows, velocities and row count
-            // go to L2 now, so that its prologue does not wait on DRAM
-            if (MODE == 0 && cw + kBW < kCells) {
-                const WarpCell wn = warp_cell(s, bp, cw + kBW);
-                if (wn.valid) {
-                    const int j0 = Rc.start[wn.rq];
-                    if (lane < Rc.cnt[wn.rq]) {
-                        const uint4* lq = reinterpret_cast<const uint4*>(s.list) + j0 + lane;
-                        prefetch_l2(lq);
-                        prefetch_l2(lq + s.npad);
-                        if (KE) {
-                            prefetch_l2(s.v + j0 + lane);
-                            prefetch_l2(s.v + s.npad + j0 + lane);
-                            prefetch_l2(s.v + 2 * s.npad + j0 + lane);
-                        }
-                    }
-                    if (lane == 0) prefetch_l2(s.cellmax + j0);
+        // the block's work items: in list mode its chunks of one species (a lane's list
+        // length depends on its species, and a warp runs to its longest list); in stencil
+        // mode its cells (the stencil is the cell's)
+        int nitems = kCells;
+        if constexpr (MODE == 0) {
+            for (int cw = w; cw < kCells; cw += kBW) {
+                const WarpCell wc = warp_cell(s, bp, cw);
+                const int cnt = wc.valid ? staged_count(Rc, wc.rq) : 0;
+                const int off = Rc.off[wc.rq];
+                int nA = 0;  // the cell's A particles come first
+                for (int t = 0; t < cnt; t += 32) {
+                    const unsigned b =
+                        __ballot_sync(FULL, t + lane < cnt && sm[off + t + lane].w == 0.f);
+                    nA += __popc(b);
+                    if (b != FULL) break;
+                }
+                if (lane == 0) {
+                    ss.c_off[cw] = off;
+                    ss.c_i0[cw] = wc.valid ? Rc.start[wc.rq] : 0;
+                    ss.c_n[cw] = cnt;
+                    ss.c_nA[cw] = nA;
                 }
             }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int na = 0, nb = 0;
+                for (int c = 0; c < kCells; ++c) {
+                    ss.prefA[c] = na;
+                    ss.prefB[c] = nb;
+                    na += ss.c_nA[c];
+                    nb += ss.c_n[c] - ss.c_nA[c];
+                }
+                ss.prefA[kCells] = na;
+                ss.prefB[kCells] = nb;
+                ss.nchA = (na + 31) >> 5;
+                ss.nch = ss.nchA + ((nb + 31) >> 5);
+            }
+            __syncthreads();
+            nitems = ss.nch;
+        }
+        for (int item = take_cell(ss, par, lane); item < nitems; item = take_cell(ss, par, lane)) {
+            WarpCell wc;
+            int i0 = 0, cnt = 32, self0 = 0;
+            if constexpr (MODE == 1) {
+                wc = warp_cell(s, bp, item);
+                i0 = wc.valid ? Rc.start[wc.rq] : 0;
+                cnt = wc.valid ? staged_count(Rc, wc.rq) : 0;
+                self0 = Rc.off[wc.rq];
+            }
             for (int ch = 0; ch * 32 < cnt; ++ch) {
-                const int li = ch * 32 + lane;
-                const bool act = li < cnt;
-                const int64_t gi = (int64_t)i0 + li;
-                const int self = self0 + li;
+                bool act;
+                int64_t gi;
+                int self;
+                if constexpr (MODE == 0) {
+                    chunk_lane(ss, item, lane, act, gi, self);
+                    // the chunk a warp takes kBW items later: its first list rows and
+                    // velocities go to L2 now, so that its prologue does not wait on DRAM
+                    if (item + kBW < nitems) {
+                        bool nact;
+                        int64_t ngi;
+                        int nself;
+                        chunk_lane(ss, item + kBW, lane, nact, ngi, nself);
+                        if (nact) {
+                            const uint4* lq = reinterpret_cast<const uint4*>(s.list) + ngi;
+                            prefetch_l2(lq);
+                            prefetch_l2(lq + s.npad);
+                            prefetch_l2(s.rows + ngi);
+                            if (KE) {
+                                prefetch_l2(s.v + ngi);
+                                prefetch_l2(s.v + s.npad + ngi);
+                                prefetch_l2(s.v + 2 * s.npad + ngi);
+                            }
+                        }
+                    }
+                } else {
+                    const int li = ch * 32 + lane;
+                    act = li < cnt;
+                    gi = (int64_t)i0 + li;
+                    self = self0 + li;
+                }
                 // issue the long-latency loads first: the first list rows, the velocity
                 const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
+                const int myrows = MODE == 0 && act ? (int)s.rows[gi] : 0;  // rows of its list
                 uint4 e0 = sent, e1 = sent, e2 = sent;
-                if (MODE == 0 && act) {
-                    e0 = __ldcs(lp);
-                    e1 = __ldcs(lp + s.npad);
-                    if (kListAhead > 2) e2 = __ldcs(lp + 2 * s.npad);
+                if (MODE == 0) {
+                    if (myrows > 0) e0 = __ldcs(lp);
+                    if (myrows > 1) e1 = __ldcs(lp + s.npad);
+                    if (kListAhead > 2 && myrows > 2) e2 = __ldcs(lp + 2 * s.npad);
                 }
                 // (the stencil loop of MODE 1 needs every register: its velocities are read
                 // after it)
@@ -698,7 +768,10 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                     v1 = s.v[s.npad + gi];
                     v2 = s.v[2 * s.npad + gi];
                 }
-                const int nkb = MODE == 0 ? s.cellmax[i0 + ch * 32] : 0;
+                int nkb = myrows;  // the warp runs to its longest list
+                if (MODE == 0)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) nkb = max(nkb, __shfl_xor_sync(FULL, nkb, o));
                 float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
                 const int si = me.w != 0.f ? 1 : 0;
                 LaneTab T;
@@ -710,9 +783,9 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                         e0 = e1;
                         if (kListAhead > 2) {
                             e1 = e2;
-                            e2 = (act && kb + 3 < nkb) ? __ldcs(lp + (int64_t)(kb + 3) * s.npad) : sent;
+                            e2 = kb + 3 < myrows ? __ldcs(lp + (int64_t)(kb + 3) * s.npad) : sent;
                         } else {
-                            e1 = (act && kb + 2 < nkb) ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
+                            e1 = kb + 2 < myrows ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
                         }
                         float near = far;
                         pair_fast<FSHIFT>(T, me, sm[lo16(e.x)], a, near);
@@ -859,19 +932,16 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                         const float vz = fmaf(h, fz, i64_to_f32_fast(v2) * pow2f(-kVelExp));
                         k = 0.5f * m * fmaf(vx, vx, fmaf(vy, vy, vz * vz));
                     }
-                    // the chunk's sum in FP64, added to its cell's (chunks of a cell run in
-                    // order on one warp)
+                    // the chunk's sum in FP64, added to the CTA's in fixed point
                     const double kc = warp_sum_d((double)k);
-                    if (lane == 0) ss.cell_ke[par][cw] += kc;
+                    if (lane == 0) atomicAdd(&ss.ke_fix, __double2ull_rn(kc * 0x1p32));
                 }
             }
         }
     });
     if (KE) {
-        // the last block's cells (every warp has passed the block's closing barrier)
-        if (threadIdx.x == 0 && blk_it > 0)
-            for (int c = 0; c < kCells; ++c) ke_cta += ss.cell_ke[(blk_it - 1) & 1][c];
-        const double acc_ke = threadIdx.x == 0 ? ke_cta : 0.0;
+        // every warp has passed the last block's closing barrier
+        const double acc_ke = threadIdx.x == 0 ? __ull2double_rn(ss.ke_fix) * 0x1p-32 : 0.0;
         block_partials(s, lb, &acc_ke, 0, 1);
     }
 }
@@ -1058,21 +1128,14 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                     row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] = pend | ((unsigned)s.smax << 16);
                     ++len;
                 }
-                int mx = len;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
-                const int nkb = (mx + 7) >> 3;
                 if (act) {
-                    // sentinel pairs up to the warp's row count: the rest of a partial row,
-                    // then whole rows (16-byte stores)
-                    int wi = len >> 1;
-                    for (; wi < nkb * 4 && (wi & 3); ++wi)
+                    // the rest of the last row holds sentinel pairs; the particle's row count
+                    // tells the force kernels where its list ends
+                    const int rows = (len + 7) >> 3;
+                    for (int wi = len >> 1; wi < rows * 4; ++wi)
                         row0[(int64_t)(wi >> 2) * rowstep + (wi & 3)] = sentpair;
-                    const uint4 sent4 = make_uint4(sentpair, sentpair, sentpair, sentpair);
-                    for (; wi < nkb * 4; wi += 4)
-                        *reinterpret_cast<uint4*>(row0 + (int64_t)(wi >> 2) * rowstep) = sent4;
+                    s.rows[gi] = (uint16_t)rows;
                 }
-                if (lane == 0) s.cellmax[i0 + ch * 32] = (uint16_t)nkb;
             }
         }
     });
@@ -1314,10 +1377,9 @@ __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
             const int si = me.sp;
             double fx = 0, fy = 0, fz = 0, u = 0, wv = 0;
             if (MODE == 0) {
-                const int nkb = s.cellmax[i0 + ch * 32];
+                const int nkb = act ? (int)s.rows[gi] : 0;  // rows of the particle's list
                 const uint4* lp = reinterpret_cast<const uint4*>(s.list) + gi;
                 for (int kb = 0; kb < nkb; ++kb) {
-                    if (!act) break;
                     uint4 e = lp[(int64_t)kb * s.npad];
                     unsigned ws[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll

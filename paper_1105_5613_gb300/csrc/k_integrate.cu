@@ -475,12 +475,7 @@ __device__ __forceinline__ int list_len(const DevSim& s, int64_t k, int nkb) {
     return len;
 }
 
-__device__ __forceinline__ int tile_nkb(const DevSim& s, int64_t k) {
-    int c = __float_as_int(s.relb[k].w) >> 1;
-    int i0 = s.cell_start[c];
-    int ch = (int)((k - i0) >> 5);
-    return s.cellmax[i0 + ch * 32];
-}
+__device__ __forceinline__ int tile_nkb(const DevSim& s, int64_t k) { return s.rows[k]; }
 
 __global__ void __launch_bounds__(kThreads) k_slot_of(DevSim s, int32_t* slot_of) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s.n;

@@ -187,7 +187,13 @@ __device__ __forceinline__ void scatter_body(const DevSim& s, int lb, int lg) {
     }
 }
 
-// Order each cell's particles by id: rank = number of smaller ids in the cell.
+// Order each cell's particles by (species, id): rank = number of smaller keys in the cell.
+// Species A first lets the force kernel form warps of one species; the order is canonical
+// (it depends only on positions, species and ids).
+__device__ __forceinline__ long long cell_key(const DevSim& s, int p) {
+    return ((long long)s.sp[p] << 32) | (long long)(unsigned)s.id[p];
+}
+
 __device__ __forceinline__ void cellsort_body(const DevSim& s, int lb, int lg) {
     if (!s.sc->rebuild) return;
     const int lane = threadIdx.x & 31;
@@ -198,19 +204,19 @@ __device__ __forceinline__ void cellsort_body(const DevSim& s, int lb, int lg) {
         int cnt = s.cell_start[c + 1] - start;
         if (cnt <= 32) {
             int pe = lane < cnt ? s.perm_tmp[start + lane] : 0;
-            int ide = lane < cnt ? s.id[pe] : 0x7fffffff;
+            long long key = lane < cnt ? cell_key(s, pe) : 0x7fffffffffffffffll;
             int rank = 0;
             for (int f = 0; f < cnt; ++f) {
-                int other = __shfl_sync(0xffffffffu, ide, f);
-                rank += other < ide;
+                long long other = __shfl_sync(0xffffffffu, key, f);
+                rank += other < key;
             }
             if (lane < cnt) s.perm[start + rank] = pe;
         } else {
             for (int e = lane; e < cnt; e += 32) {
                 int pe = s.perm_tmp[start + e];
-                int ide = s.id[pe];
+                long long key = cell_key(s, pe);
                 int rank = 0;
-                for (int f = 0; f < cnt; ++f) rank += s.id[s.perm_tmp[start + f]] < ide;
+                for (int f = 0; f < cnt; ++f) rank += cell_key(s, s.perm_tmp[start + f]) < key;
                 s.perm[start + rank] = pe;
             }
         }

@@ -32,6 +32,7 @@ struct bbmd_sim {
     double* ref[BBMD_MAX_ORIGINS] = {};  // unwrapped positions by id of each time origin
     int sticky = 0;
     int device = 0;                  // CUDA device of the handle (current at creation)
+    double last_dt = -1.0;           // dt of the last step call (its closing kick may be pending)
     int nsm = 1;
     int graph_gen = 0;               // bumped whenever captured launch arguments go stale
     long long tune_step = 0, tune_rebuilds = 0;  // counters at the last shape tuning
@@ -275,6 +276,7 @@ void apply_shape(bbmd_sim* sim, int bz) {
 
 bbmd_status rebuild_now(bbmd_sim* sim);
 bbmd_status refresh_forces_and_K(bbmd_sim* sim);
+void finish_velocities(bbmd_sim* sim);
 void free_graphs(bbmd_sim* sim);
 
 // A list build cut some lists at the capacity (Verlet mode).  The steps since then took
@@ -302,18 +304,24 @@ bbmd_status grow_lists(bbmd_sim* sim) {
         const int cleared = st & ~ST_LIST_OVERFLOW;
         CK(cudaMemcpyAsync(&D.sc->status, &cleared, sizeof(int), cudaMemcpyHostToDevice, sim->st));
         CK(cudaStreamSynchronize(sim->st));  // `cleared` lives on this stack frame
+        finish_velocities(sim);  // the pending kick used the forces about to be recomputed
         rebuild_now(sim);
         refresh_forces_and_K(sim);
     }
     return BBMD_OK;
 }
 
-bbmd_status read_status(bbmd_sim* sim) {
-    bbmd_status g = grow_lists(sim);
-    if (g != BBMD_OK) return g;
-    int st = 0;
-    CK(cudaMemcpyAsync(&st, &sim->d.sc->status, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
-    CK(cudaStreamSynchronize(sim->st));
+// The status word: grow cut lists if needed, then report the sticky bits.  `known`: the
+// status word the caller has just read after synchronising (skips two round trips unless
+// lists were cut), or -1.
+bbmd_status read_status(bbmd_sim* sim, int known = -1) {
+    int st = known;
+    if (known < 0 || (known & ST_LIST_OVERFLOW)) {
+        bbmd_status g = grow_lists(sim);
+        if (g != BBMD_OK) return g;
+        CK(cudaMemcpyAsync(&st, &sim->d.sc->status, sizeof(int), cudaMemcpyDeviceToHost, sim->st));
+        CK(cudaStreamSynchronize(sim->st));
+    }
     sim->sticky |= st;
     if (sim->sticky & (ST_LIST_OVERFLOW | ST_STENCIL_OVERFLOW))
         return fail(sim, BBMD_ERR_LIST_OVERFLOW,
@@ -430,6 +438,18 @@ void free_graphs(bbmd_sim* sim) {
             g = nullptr;
         }
 }
+
+// Start of a step call: the closing half kick a previous call left pending is carried into
+// this call's first update when dt is unchanged; otherwise it is applied now.
+void begin_call(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* th) {
+    if (dt != sim->last_dt) launch_finish(sim->d, sim->st);
+    launch_begin(sim->d, sim->st, nsteps, dt, th);
+    sim->last_dt = dt;
+}
+
+// Apply a pending closing half kick to the stored velocities (before velocities are read
+// out or replaced, or positions move outside a step).
+void finish_velocities(bbmd_sim* sim) { launch_finish(sim->d, sim->st); }
 
 bbmd_status build_graph(bbmd_sim* sim, int nh) {
     cudaGraph_t g;
@@ -692,7 +712,7 @@ bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt, const b
     double acc[BBMD_PHASE_COUNT] = {0, 0, 0, 0, 0};
     DevScalars scl0;
     CK(cudaMemcpyAsync(&scl0, sim->d.sc, sizeof(scl0), cudaMemcpyDeviceToHost, sim->st));
-    launch_begin(sim->d, sim->st, nsteps, dt, nh ? th : nullptr);
+    begin_call(sim, nsteps, dt, nh ? th : nullptr);
     for (int64_t k = 0; k < nsteps; ++k) {
         CK(cudaEventRecord(ev[0], sim->st));
         launch_integrate(sim->d, sim->st);
@@ -714,8 +734,6 @@ bbmd_status bbmd_step_profiled(bbmd_sim* sim, int64_t nsteps, double dt, const b
             acc[q] += t;
         }
     }
-    launch_finish(sim->d, sim->st);
-    LAUNCHED("finish");
     DevScalars scl1;
     CK(cudaMemcpyAsync(&scl1, sim->d.sc, sizeof(scl1), cudaMemcpyDeviceToHost, sim->st));
     CK(cudaStreamSynchronize(sim->st));
@@ -746,11 +764,9 @@ bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_therm
         bbmd_status r = build_graph(sim, nh);
         if (r != BBMD_OK) return r;
     }
-    launch_begin(sim->d, sim->st, nsteps, dt, nh ? th : nullptr);
+    begin_call(sim, nsteps, dt, nh ? th : nullptr);
     LAUNCHED("begin");
     for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(sim->graph[nh], sim->st));
-    launch_finish(sim->d, sim->st);
-    LAUNCHED("finish");
     return BBMD_OK;
 }
 
@@ -815,7 +831,7 @@ bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args
     CK(cudaMemcpyAsync(h, sim->dout, sizeof(h), cudaMemcpyDeviceToHost, sim->st));
     CK(cudaMemcpyAsync(&scl, D.sc, sizeof(scl), cudaMemcpyDeviceToHost, sim->st));
     CK(cudaStreamSynchronize(sim->st));
-    bbmd_status rs = read_status(sim);
+    bbmd_status rs = read_status(sim, scl.status);
     if (rs != BBMD_OK) return rs;
     double Vol = sim->box[0] * sim->box[1] * sim->box[2];
     double g = (double)(3 * D.n - 3);
@@ -875,6 +891,7 @@ bbmd_status bbmd_observe(bbmd_sim* sim, uint32_t mask, const bbmd_obs_args* args
 bbmd_status bbmd_minimize(bbmd_sim* sim, int64_t nsteps, double hmax, double dmax) {
     if (!sim || nsteps < 0 || !(hmax > 0.0) || !(dmax > 0.0)) return BBMD_ERR_ARG;
     DeviceGuard dg(sim->device);
+    finish_velocities(sim);
     for (int64_t k = 0; k < nsteps; ++k) {
         launch_force(sim->d, sim->st, false, false);
         launch_sd_step(sim->d, sim->st, hmax, dmax);
@@ -890,6 +907,7 @@ bbmd_status bbmd_minimize(bbmd_sim* sim, int64_t nsteps, double hmax, double dma
 bbmd_status bbmd_get_state(bbmd_sim* sim, double* pos, double* vel, int32_t* image) {
     if (!sim) return BBMD_ERR_ARG;
     DeviceGuard dg(sim->device);
+    finish_velocities(sim);
     const int64_t n = sim->d.n;
     double* tp = pos ? (double*)dev_alloc(sim, 3 * n * 8) : nullptr;
     double* tv = vel ? (double*)dev_alloc(sim, 3 * n * 8) : nullptr;
@@ -918,6 +936,7 @@ bbmd_status bbmd_set_state(bbmd_sim* sim, const double* pos, const double* vel,
                            const int32_t* image) {
     if (!sim || !pos || !vel) return BBMD_ERR_ARG;
     DeviceGuard dg(sim->device);
+    finish_velocities(sim);
     const int64_t n = sim->d.n;
     double* tp = (double*)dev_alloc(sim, 3 * n * 8);
     double* tv = (double*)dev_alloc(sim, 3 * n * 8);
@@ -1107,6 +1126,7 @@ bbmd_status bbmd_get_neighbors(bbmd_sim* sim, const int64_t* ids, int64_t m, int
 bbmd_status bbmd_tune(bbmd_sim* sim) {
     if (!sim) return BBMD_ERR_ARG;
     DeviceGuard dg(sim->device);
+    finish_velocities(sim);
     if (sim->shapes.size() < 2) return BBMD_OK;
     // weight of the list build: the rebuilds per step seen since the last tuning (a rebuild
     // about every four steps when fewer than 20 steps were taken)
@@ -1129,6 +1149,7 @@ bbmd_status bbmd_tune(bbmd_sim* sim) {
 bbmd_status bbmd_rebuild(bbmd_sim* sim) {
     if (!sim) return BBMD_ERR_ARG;
     DeviceGuard dg(sim->device);
+    finish_velocities(sim);
     bbmd_status rc = rebuild_now(sim);
     if (rc != BBMD_OK) return rc;
     launch_force(sim->d, sim->st, false, false);
@@ -1568,7 +1589,7 @@ bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd
         }
         const bool fshift = b->rep[0]->d.pt.shift == BBMD_SHIFT_FORCE;
         for (size_t r = 0; r < b->rep.size(); ++r)
-            launch_begin(b->rep[r]->d, b->st, nsteps, dt, nh ? &th[r] : nullptr);
+            begin_call(b->rep[r], nsteps, dt, nh ? &th[r] : nullptr);
         // the abort flag is cleared once per call, the queue head and the finished counts
         // before every launch; a launch runs up to kPersistSteps steps (the queue counts
         // items of one launch in 32 bits)
@@ -1584,7 +1605,6 @@ bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd
                 e = BBMD_PERSIST_NS::launch_persistent_step(a, b->pgrid, b->psmax, nh != 0, fshift, b->st);
             if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
         }
-        for (size_t r = 0; r < b->rep.size(); ++r) launch_finish(b->rep[r]->d, b->st);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
         return BBMD_OK;
@@ -1597,12 +1617,11 @@ bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd
         if (rc != BBMD_OK) return rc;
     }
     for (size_t r = 0; r < b->rep.size(); ++r)
-        launch_begin(b->rep[r]->d, b->st, nsteps, dt, nh ? &th[r] : nullptr);
+        begin_call(b->rep[r], nsteps, dt, nh ? &th[r] : nullptr);
     for (int64_t k = 0; k < nsteps; ++k) {
         cudaError_t e = cudaGraphLaunch(b->graph[nh], b->st);
         if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
     }
-    for (size_t r = 0; r < b->rep.size(); ++r) launch_finish(b->rep[r]->d, b->st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return batch_fail(b, BBMD_ERR_CUDA, cudaGetErrorString(e));
     return BBMD_OK;

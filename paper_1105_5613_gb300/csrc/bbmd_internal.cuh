@@ -49,7 +49,10 @@ struct DevScalars {
     double kin_last;         // K of the last finalize (before NH scaling)
     double maxf;             // steepest descent: max |F|
     long long step, n_rebuilds;
-    int step_in_call, n_in_call, kind, pending;
+    int step_in_call, n_in_call, kind;
+    int pending;             // 1: the last step's closing half kick (scaled by s_end) is not
+                             //    yet in the stored velocities (applied by the next call's
+                             //    first update, or by the finish kernel)
     int rebuild;             // 1: the gated rebuild kernels run in this step
     int near;                // 1: some displacement of this step exceeds half the threshold
     int status;              // ST_* bits
@@ -341,6 +344,7 @@ void launch_begin(const DevSim& s, cudaStream_t st, int64_t nsteps, double dt,
                   const bbmd_thermostat* th);
 void launch_integrate(const DevSim& s, cudaStream_t st);
 void launch_finalize(const DevSim& s, cudaStream_t st, bool ke);
+// apply the closing half kick and NH scale a call left pending (no-op when none is)
 void launch_finish(const DevSim& s, cudaStream_t st);
 void launch_state_sums(const DevSim& s, cudaStream_t st);          // KE, P partials -> sc->K etc.
 void launch_reduce_partials(const DevSim& s, cudaStream_t st, int nq, double* out_dev);

@@ -490,8 +490,13 @@ __device__ __forceinline__ void stencil_run(const Region& R, const WarpCell& wc,
 // The reach carries a relative margin of 2^-9. Against it, FP32 rounding of the staged
 // coordinates and of the box distance (about 1e-6 relative) is negligible. A dropped
 // candidate lies beyond the upper edge of the exact-test band for every lane.
-constexpr int kRing = 256;      // ring entries per warp (a power of two)
-constexpr int kRingWords = 4;   // 32-candidate words tested per pass
+#ifndef BBMD_RING_WORDS
+#define BBMD_RING_WORDS 4
+#endif
+constexpr int kRingWords = BBMD_RING_WORDS;   // 32-candidate words tested per pass
+// ring entries per warp: twice a pass (a pass's words then lie in one half, contiguous)
+constexpr int kRing = 64 * kRingWords;
+static_assert(kRingWords == 4 || kRingWords == 8, "a pass of 4 or 8 words");
 
 struct WarpBox {
     float lo[3], hi[3];

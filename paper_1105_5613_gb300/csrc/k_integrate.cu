@@ -28,9 +28,16 @@ constexpr unsigned FULL = 0xffffffffu;
 
 #include "step_bodies.cuh"
 
+// Start of a call.  If the previous call's closing half kick and Nose-Hoover scale are
+// still pending (the velocities were not finished: sc->pending), they are carried into
+// the first velocity update of this call, which applies s_end (v + h F) and this call's
+// scale and first half kick in one increment; the host carries only when dt is unchanged
+// (the pending kick and the first kick use the same h).
 __global__ void k_begin(DevSim s, int64_t nsteps, double dt, int kind, double T0, double T1,
                         double tau) {
     DevScalars* sc = s.sc;
+    const bool carry = sc->pending != 0;
+    const double s_carry = carry ? sc->s_end : 1.0;
     sc->dt = dt;
     sc->hdt[0] = (float)(0.5 * dt / s.pt.dmass[0]);
     sc->hdt[1] = (float)(0.5 * dt / s.pt.dmass[1]);
@@ -40,15 +47,15 @@ __global__ void k_begin(DevSim s, int64_t nsteps, double dt, int kind, double T0
     sc->T_start = T0;
     sc->T_end = T1;
     sc->tau = tau;
-    sc->pending = 0;
+    sc->pending = carry ? 1 : 0;
     sc->g = (double)(3 * s.n - 3);
     if (kind == BBMD_THERMO_NH) {
         double Kout;
-        sc->s_next = nh_half(sc, sc->K, ramp_T(sc, 0), dt, &Kout);
+        sc->s_next = nh_half(sc, sc->K, ramp_T(sc, 0), dt, &Kout) * s_carry;
         sc->K = Kout;
         sc->T_last = ramp_T(sc, 0);
     } else {
-        sc->s_next = 1.0;
+        sc->s_next = s_carry;
     }
     sc->s_end = 1.0;
 }
@@ -78,51 +85,70 @@ __global__ void __launch_bounds__(256) k_finalize_many(ManySims m, int ke) {
     finalize_body(sh, ke);
 }
 
+// The finished velocity of particle i: the pending closing half kick and Nose-Hoover
+// scale of the last call applied, v + round(s_end (v + h F) - v) (the arithmetic of the
+// closing update), or the stored velocity when nothing is pending.
 template <bool FP64>
-__global__ void __launch_bounds__(kThreads) k_finish(DevSim s) {
+__device__ __forceinline__ void finished_velocity(const DevSim& s, int64_t i, long long vo[3]) {
     const DevScalars* sc = s.sc;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) vo[d] = s.v[d * s.npad + i];
+    if (!sc->pending) return;
     const double dt = sc->dt;
     const double se = sc->s_end;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int spc = s.sp[i];
-        if (!FP64) {
-            float4 F = s.F[i];
-            float Fv[3] = {F.x, F.y, F.z};
-            float h = 0.5f * (float)dt / s.pt.mass[spc];
-            float sm1 = (float)(se - 1.0);
-            float sf = (float)se;
+    const int spc = s.sp[i];
+    if (!FP64) {
+        const float4 F = s.F[i];
+        const float Fv[3] = {F.x, F.y, F.z};
+        const float h = 0.5f * (float)dt / s.pt.mass[spc];
+        const float sm1 = (float)(se - 1.0);
+        const float sf = (float)se;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                int64_t idx = d * s.npad + i;
-                long long v = s.v[idx];
-                float vf = i64_to_f32_fast(v) * pow2f(-kVelExp);
-                float dv = fmaf(sm1, vf, sf * h * Fv[d]);
-                s.v[idx] = v + f32_to_i64(dv * pow2f(kVelExp));
-            }
-        } else {
-            double h = 0.5 * dt / s.pt.dmass[spc];
+        for (int d = 0; d < 3; ++d) {
+            const float vf = i64_to_f32_fast(vo[d]) * pow2f(-kVelExp);
+            const float dv = fmaf(sm1, vf, sf * h * Fv[d]);
+            vo[d] += f32_to_i64(dv * pow2f(kVelExp));
+        }
+    } else {
+        const double h = 0.5 * dt / s.pt.dmass[spc];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                int64_t idx = d * s.npad + i;
-                long long v = s.v[idx];
-                double vd = __ll2double_rn(v) * 0x1p-52;
-                double dv = (se - 1.0) * vd + se * h * s.Fd[idx];
-                s.v[idx] = v + __double2ll_rn(dv * 0x1p52);
-            }
+        for (int d = 0; d < 3; ++d) {
+            const double vd = __ll2double_rn(vo[d]) * 0x1p-52;
+            const double dv = (se - 1.0) * vd + se * h * s.Fd[d * s.npad + i];
+            vo[d] += __double2ll_rn(dv * 0x1p52);
         }
     }
 }
 
-// Kinetic energy and momentum of the stored velocities (FP64) -> partials 0..3.
+// Apply the pending closing update to the stored velocities (nothing when none is pending;
+// k_finish_done then marks the velocities finished).
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_finish(DevSim s) {
+    if (!s.sc->pending) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        long long vo[3];
+        finished_velocity<FP64>(s, i, vo);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s.v[d * s.npad + i] = vo[d];
+    }
+}
+
+__global__ void k_finish_done(DevSim s) { s.sc->pending = 0; }
+
+// Kinetic energy and momentum (FP64) of the finished velocities (the stored ones with any
+// pending closing update applied on the fly, as the finish kernel would) -> partials 0..3.
+template <bool FP64>
 __global__ void __launch_bounds__(kThreads) k_state_sums(DevSim s) {
     double k = 0, px = 0, py = 0, pz = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double m = s.pt.dmass[s.sp[i]];
-        double vx = __ll2double_rn(s.v[i]) * 0x1p-52;
-        double vy = __ll2double_rn(s.v[s.npad + i]) * 0x1p-52;
-        double vz = __ll2double_rn(s.v[2 * s.npad + i]) * 0x1p-52;
+        long long vo[3];
+        finished_velocity<FP64>(s, i, vo);
+        double vx = __ll2double_rn(vo[0]) * 0x1p-52;
+        double vy = __ll2double_rn(vo[1]) * 0x1p-52;
+        double vz = __ll2double_rn(vo[2]) * 0x1p-52;
         k += 0.5 * m * (vx * vx + vy * vy + vz * vz);
         px += m * vx;
         py += m * vy;
@@ -621,10 +647,14 @@ void launch_finish(const DevSim& s, cudaStream_t st) {
         k_finish<true><<<s.grid_part, kThreads, 0, st>>>(s);
     else
         k_finish<false><<<s.grid_part, kThreads, 0, st>>>(s);
+    k_finish_done<<<1, 1, 0, st>>>(s);
 }
 
 void launch_state_sums(const DevSim& s, cudaStream_t st) {
-    k_state_sums<<<s.grid_part, kThreads, 0, st>>>(s);
+    if (s.precision == BBMD_PREC_FP64)
+        k_state_sums<true><<<s.grid_part, kThreads, 0, st>>>(s);
+    else
+        k_state_sums<false><<<s.grid_part, kThreads, 0, st>>>(s);
 }
 
 void launch_reduce_partials(const DevSim& s, cudaStream_t st, int nq, double* out_dev) {

@@ -184,6 +184,45 @@ def test_trajectory_split_calls_equal_one_call():
     b.close()
 
 
+def test_nose_hoover_split_calls_equal_one_call():
+    # the closing half kick and thermostat scale of a call are carried into the next
+    # call's first update (same dt), exactly as between two steps of one call; an observe
+    # between the calls leaves the state alone
+    a, n, L, pos, vel, sp, p = make(ncell=8, shake=0.05)
+    p.block_z = a.info()["block_z"]
+    b = bbmd.Sim(p, n, L, sp, pos, vel)
+    th = (bbmd.THERMO_NH, 0.9, 0.9, 0.5)
+    a.step(60, 0.005, th)
+    for _ in range(6):
+        b.step(10, 0.005, th)
+        b.observe(bbmd.OBS_ENERGY)
+    pa, va, _ = a.get_state()
+    pb, vb, _ = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    assert a.observe(bbmd.OBS_ENERGY)["xi"] == b.observe(bbmd.OBS_ENERGY)["xi"]
+    a.close()
+    b.close()
+
+
+def test_dt_change_between_calls_finishes_the_last_step():
+    # a new dt applies the pending closing kick first: the same state as reading the
+    # velocities out between the calls
+    a, n, L, pos, vel, sp, p = make(ncell=8, shake=0.05)
+    p.block_z = a.info()["block_z"]
+    b = bbmd.Sim(p, n, L, sp, pos, vel)
+    th = (bbmd.THERMO_NH, 0.9, 0.9, 0.5)
+    a.step(10, 0.005, th)
+    a.step(10, 0.004, th)
+    b.step(10, 0.005, th)
+    b.get_state()
+    b.step(10, 0.004, th)
+    pa, va, _ = a.get_state()
+    pb, vb, _ = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("prec,tol", [(0, 1e-4), (1, 1e-9)])
 def test_trajectory_nose_hoover_100_steps(prec, tol, model):

@@ -278,9 +278,6 @@ __device__ bool finish_block(const DevSim& s, const Region& R, float4* sm, uint6
     return true;
 }
 
-#ifndef BBMD_CELL_PAIRWORDS
-#define BBMD_CELL_PAIRWORDS 1
-#endif
 #ifndef BBMD_STAGE_BUFFERS
 #define BBMD_STAGE_BUFFERS 1  // 2: stage block i+1 while block i is computed
 #endif
@@ -413,6 +410,21 @@ __device__ __forceinline__ void pair_add(const LaneTab& T, bool b, float dx, flo
     a.fz = fmaf(f, dz, a.fz);
 }
 
+// Force of one interacting pair with the constants of its species pair given (the stencil
+// kernel loads them per candidate stream); the same arithmetic as pair_add.
+template <bool FSHIFT>
+__device__ __forceinline__ void pair_add_c(float sig2, float e48, float cpot, float fc, float dx, float dy,
+                                           float dz, float r2, Acc& a) {
+    float ir2 = rcp_approx(r2);
+    float s2 = sig2 * ir2;
+    float s6 = s2 * s2 * s2;
+    float f = e48 * ir2 * s6 * (s6 - cpot);
+    if (FSHIFT) f = fmaf(fc, rsqrtf(r2), f);
+    a.fx = fmaf(f, dx, a.fx);
+    a.fy = fmaf(f, dy, a.fy);
+    a.fz = fmaf(f, dz, a.fz);
+}
+
 // Fast path of one list pair (i, staged t), classified by d = r^2 - (middle of the band
 // around rc^2 for the species of j): interacting iff d <= -hw; |d| < hw is the band,
 // left to the exact fix-up; the smallest |d| of a batch tells whether it has band pairs.
@@ -432,11 +444,19 @@ __device__ __forceinline__ bool min_image_copy(const DevSim& s, float dx, float 
     return fabsf(dx) < s.halfL[0] && fabsf(dy) < s.halfL[1] && fabsf(dz) < s.halfL[2];
 }
 
-// Exact decision for a band pair; adds its force if the FP64 rule says it interacts.
-// Kept out of line: it runs for a few pairs per million and must not add register
-// pressure to the batch loop.
+// Exact decision for a band pair; adds its force if the FP64 rule says it interacts.  It
+// runs for a few pairs per million.  Called out of line (pair_band_call), it keeps the
+// lane's pair constants and accumulators in local memory (a stack frame); inline, it
+// costs registers.  Inline is faster where the list kernel has 128 registers a thread
+// (2 x 2 x 4 and 2 x 2 x 8: 6 % at 2 M particles); out of line where it has fewer
+// (2 x 2 x 1 and 2 x 2 x 2: inline is 20 % slower there), and in the persistent batch
+// kernel, whose other phases share the register budget (inline, some of its forms spill).
+#ifndef BBMD_BAND_INLINE
+#define BBMD_BAND_INLINE (BBMD_BLOCK_Z >= 4)
+#endif
+constexpr bool kBandInline = BBMD_BAND_INLINE;
 template <bool FSHIFT>
-__device__ __noinline__ void pair_band(const DevSim& s, const Region& R, const LaneTab& T, float4 me, float4 p,
+__device__ __forceinline__ void pair_band(const DevSim& s, const Region& R, const LaneTab& T, float4 me, float4 p,
                           int t, int64_t gi, bool valid, Acc& a) {
     float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -446,6 +466,12 @@ __device__ __noinline__ void pair_band(const DevSim& s, const Region& R, const L
     int64_t gj = staged_global(R, t);
     if (r2_exact(s, gi, gj) < s.pt.rc2[T.si * 2 + (b ? 1 : 0)])
         pair_add<FSHIFT>(T, b, dx, dy, dz, r2, true, a);
+}
+
+template <bool FSHIFT>
+__device__ __noinline__ void pair_band_call(const DevSim& s, const Region& R, const LaneTab& T, float4 me,
+                                            float4 p, int t, int64_t gi, bool valid, Acc& a) {
+    pair_band<FSHIFT>(s, R, T, me, p, t, gi, valid, a);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -485,18 +511,11 @@ __device__ __forceinline__ void stencil_run(const Region& R, const WarpCell& wc,
 // ------------------------------------------------------- stencil compaction ----
 // A stencil candidate farther than the reach from the bounding box of the warp's particles
 // pairs with none of them.  Such candidates are dropped, 32 at a time, before the per-lane
-// tests. The survivors keep their stencil order in a per-warp ring of staged indices. The
-// lists and force sums therefore come out exactly as when every candidate is tested.
+// tests. The survivors keep their stencil order within their species' stream (below). The
+// lists and force sums therefore hold exactly the pairs that testing every candidate finds.
 // The reach carries a relative margin of 2^-9. Against it, FP32 rounding of the staged
 // coordinates and of the box distance (about 1e-6 relative) is negligible. A dropped
 // candidate lies beyond the upper edge of the exact-test band for every lane.
-#ifndef BBMD_RING_WORDS
-#define BBMD_RING_WORDS 4
-#endif
-constexpr int kRingWords = BBMD_RING_WORDS;   // 32-candidate words tested per pass
-// ring entries per warp: twice a pass (a pass's words then lie in one half, contiguous)
-constexpr int kRing = 64 * kRingWords;
-static_assert(kRingWords == 4 || kRingWords == 8, "a pass of 4 or 8 words");
 
 struct WarpBox {
     float lo[3], hi[3];
@@ -558,11 +577,6 @@ __device__ __forceinline__ StageShared& stage_shared() {
     return ss;
 }
 
-__device__ __forceinline__ uint32_t* warp_ring(int w) {
-    __shared__ __align__(16) uint32_t ring_all[kBW][kRing];
-    return ring_all[w];
-}
-
 // Bounding box of the active lanes' positions.
 __device__ __forceinline__ WarpBox warp_box(float4 me, bool act) {
     WarpBox b;
@@ -598,40 +612,104 @@ __device__ __forceinline__ bool scan_next(const Region& R, const WarpCell& wc, S
     return true;
 }
 
-// Candidates g0 + lane (below re) go through the box test; survivors are appended to the
-// ring at stream positions fill, fill + 1, ... in candidate order.  cself receives the
-// stream position of the lane's own particle when its group passes.
-__device__ __forceinline__ void compact_group(const float4* sm, int g0, int re, const WarpBox& bx,
-                                              float keepA, float keepB, uint32_t* ring, int& fill,
-                                              int self, int& cself, int lane) {
-    const int t = g0 + lane;
-    bool keep = false;
-    if (t < re) {
-        const float4 p = sm[t];
-        const float ex = fmaxf(fmaxf(bx.lo[0] - p.x, p.x - bx.hi[0]), 0.f);
-        const float ey = fmaxf(fmaxf(bx.lo[1] - p.y, p.y - bx.hi[1]), 0.f);
-        const float ez = fmaxf(fmaxf(bx.lo[2] - p.z, p.z - bx.hi[2]), 0.f);
-        keep = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < (p.w != 0.f ? keepB : keepA);
-    }
-    const unsigned bal = __ballot_sync(FULL, keep);
-    const int pos = fill + __popc(bal & ((1u << lane) - 1u));
-    if (keep) ring[pos & (kRing - 1)] = (uint32_t)t;
-    const int src = self - g0;
-    const int sp = __shfl_sync(FULL, pos, src & 31);
-    if (src >= 0 && src < 32) cself = sp;
-    fill += __popc(bal);
-}
-
-// After the last group: the rest of the last word points at the far sentinel record.
-__device__ __forceinline__ void ring_pad(uint32_t* ring, int fill, int lane, uint32_t sentinel) {
-    const int pe = (fill + 31) & ~31;
-    if (fill + lane < pe) ring[(fill + lane) & (kRing - 1)] = sentinel;
-}
-
 // Squared reach from the box for a candidate of species 0 / 1: the largest upper band edge
 // over the lane species, widened by 2^-9.
 __device__ __forceinline__ float keep_reach(const float* hi4, int sj) {
     return fmaxf(hi4[sj], hi4[2 + sj]) * (1.0f + 0x1p-9f);
+}
+
+// ------------------------------------------------- species-split candidate streams ----
+// The list build compacts the stencil candidates within reach of the warp's box into two
+// streams, one per species of the candidate.  An entry holds the candidate relative to the
+// box centre c, p' = p - c, and q = |p'|^2; a parallel ring holds its staged index.  A
+// lane (m' = its own position - c) then tests a candidate of stream S as
+//     r^2 - R^2(s_i, S) = q + (|m'|^2 - R^2(s_i, S)) - 2 p'.m'
+// (an add and three FMAs after one broadcast load; the threshold is the same for the
+// whole stream).  Relative to the box centre, |p'| stays below the box half-diagonal plus
+// the reach (about 6 cell sides' worth of r^2 at most), so the FP32 error of this form is
+// about 1e-5 in r^2, below the margin of the exact-test band (the band's edges lie at a
+// relative 1e-5 and 3e-5 from R^2, about 8e-5 and 2.4e-4 at the bench's R^2 = 7.84).
+// The band test uses the same form, so the candidates it sends to the exact rule are
+// exactly those whose FP32 value could be on the wrong side.
+constexpr int kSRing = 64;  // entries per stream ring (two 32-entry words; a power of two)
+
+struct StreamRings {
+    float4 rec[2][kSRing];     // (p' - c, q)
+    uint16_t idx[2][kSRing];   // staged index
+    float4 box[2];             // (c, reach^2 of species A), (half-extents, reach^2 of B)
+};
+
+__device__ __forceinline__ StreamRings& warp_streams(int w) {
+    __shared__ __align__(16) StreamRings rings_all[kBW];
+    return rings_all[w];
+}
+
+// The warp's box as centre and half-extents, kept with the reaches in the warp's
+// shared-memory slot (the compaction reads them there: fewer live registers); returns the
+// centre.
+__device__ __forceinline__ float4 warp_frame(const WarpBox& b, float keepA, float keepB, StreamRings& SR,
+                                             int lane) {
+    const float4 c = make_float4(0.5f * (b.lo[0] + b.hi[0]), 0.5f * (b.lo[1] + b.hi[1]),
+                                 0.5f * (b.lo[2] + b.hi[2]), keepA);
+    if (lane == 0) {
+        SR.box[0] = c;
+        SR.box[1] = make_float4(0.5f * (b.hi[0] - b.lo[0]), 0.5f * (b.hi[1] - b.lo[1]),
+                                0.5f * (b.hi[2] - b.lo[2]), keepB);
+    }
+    __syncwarp();
+    return c;
+}
+
+// Candidates g0 + lane (below re) go through the box test (against the centred box, with
+// the reach of the candidate's species); survivors are appended to their species' stream
+// at positions fill[S], fill[S] + 1, ... in candidate order.  cself receives the stream
+// position of the lane's own particle (in the stream of its own species) when its group
+// passes.
+__device__ __forceinline__ void compact_streams(const float4* sm, int g0, int re, StreamRings& SR,
+                                                int fill[2], int self, int& cself, int lane) {
+    const int t = g0 + lane;
+    bool keep = false;
+    int sj = 0;
+    float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < re) {
+        const float4 p = sm[t];
+        const float4 c = SR.box[0], h = SR.box[1];
+        const float x = p.x - c.x, y = p.y - c.y, z = p.z - c.z;
+        const float ex = fmaxf(fabsf(x) - h.x, 0.f);
+        const float ey = fmaxf(fabsf(y) - h.y, 0.f);
+        const float ez = fmaxf(fabsf(z) - h.z, 0.f);
+        sj = p.w != 0.f ? 1 : 0;
+        keep = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < (sj ? h.w : c.w);
+        rec = make_float4(x, y, z, fmaf(z, z, fmaf(y, y, x * x)));
+    }
+    const unsigned bA = __ballot_sync(FULL, keep && sj == 0);
+    const unsigned bB = __ballot_sync(FULL, keep && sj == 1);
+    const unsigned lt = (1u << lane) - 1u;
+    const int pos = sj ? fill[1] + __popc(bB & lt) : fill[0] + __popc(bA & lt);
+    if (keep) {
+        SR.rec[sj][pos & (kSRing - 1)] = rec;
+        SR.idx[sj][pos & (kSRing - 1)] = (uint16_t)t;
+    }
+    const int src = self - g0;
+    const int sp = __shfl_sync(FULL, pos, src & 31);
+    if (src >= 0 && src < 32) cself = sp;
+    fill[0] += __popc(bA);
+    fill[1] += __popc(bB);
+}
+
+// After the last group: the rest of stream S's last word holds far records (q huge, so
+// every test is positive) pointing at the sentinel.
+__device__ __forceinline__ void stream_pad(StreamRings& SR, int S, int fill, int lane, int sentinel) {
+    const int pe = (fill + 31) & ~31;
+    if (fill + lane < pe) {
+        SR.rec[S][(fill + lane) & (kSRing - 1)] = make_float4(kFar, kFar, kFar, 3.0f * kFar * kFar);
+        SR.idx[S][(fill + lane) & (kSRing - 1)] = (uint16_t)sentinel;
+    }
+}
+
+// r^2 - R^2 of a stream entry for a lane: m2 = -2 m', cst = |m'|^2 - R^2(s_i, S).
+__device__ __forceinline__ float stream_d(const float4 r, float m2x, float m2y, float m2z, float cst) {
+    return fmaf(r.z, m2z, fmaf(r.y, m2y, fmaf(r.x, m2x, r.w + cst)));
 }
 
 // Which force kernel runs: in cell mode the stencil kernel (MODE 1); in Verlet mode the
@@ -644,7 +722,8 @@ __device__ __forceinline__ bool force_selected(const DevSim& s) {
 }
 
 // MODE 0: Verlet list.  MODE 1: every particle of the 27-cell stencil (no stored list).
-template <int MODE, bool KE, bool FSHIFT>
+// BAND_INL: the band fix-up inline (else called out of line).
+template <int MODE, bool KE, bool FSHIFT, bool BAND_INL = kBandInline>
 __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     if (!force_selected<MODE>(s)) return;  // CTA-uniform, before any barrier
     extern __shared__ float4 smem[];
@@ -668,8 +747,8 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
     const float far = kFar;
     const unsigned sv = (unsigned)s.smax | ((unsigned)s.smax << 16);
     const uint4 sent = make_uint4(sv, sv, sv, sv);
-    uint32_t* ring = nullptr;  // candidate ring of the stencil mode
-    if constexpr (MODE == 1) ring = warp_ring(w);
+    StreamRings* SRp = nullptr;  // candidate streams of the stencil mode
+    if constexpr (MODE == 1) SRp = &warp_streams(w);
     for_each_block(s, lb, lg, smem, s.smax + 1, R, mbar,
                    [&](const BlockPos& bp, const Region& Rc,
                                                       const float4* sm) {
@@ -780,7 +859,7 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                 float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
                 const int si = me.w != 0.f ? 1 : 0;
                 LaneTab T;
-                load_tab(s, si, T);
+                if constexpr (MODE == 0) load_tab(s, si, T);
                 Acc a = {0.f, 0.f, 0.f};
                 if (MODE == 0) {
                     for (int kb = 0; kb < nkb; ++kb) {
@@ -806,116 +885,114 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                             const unsigned ws[4] = {e.x, e.y, e.z, e.w};
                             for (int q = 0; q < 8; ++q) {
                                 int t = (q & 1) ? hi16(ws[q >> 1]) : lo16(ws[q >> 1]);
-                                pair_band<FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
+                                if constexpr (BAND_INL)
+                                    pair_band<FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
+                                else
+                                    pair_band_call<FSHIFT>(s, Rc, T, me, sm[t], t, gi, true, a);
                             }
                         }
                     }
                 } else {
-                    // the stencil on the fly: the candidates within reach of the warp's box,
-                    // 32 at a time, are filtered against the cutoff into a bitmask (as the
-                    // list build does against rc + skin), band candidates decided by the
-                    // exact rule, then the forces of the set bits are added
-                    const float rcA = T.rlo0, drc = T.rlo1 - T.rlo0;
-                    const float bandc = fmaxf(T.rhi0 - T.rlo0, T.rhi1 - T.rlo1);
-                    const WarpBox bx = warp_box(me, act);
-                    const float keepA = keep_reach(s.pt.rc2hi, 0), keepB = keep_reach(s.pt.rc2hi, 1);
-                    int fill = 0, done = 0, cself = -1;
+                    // the stencil on the fly: the candidates within reach of the warp's box
+                    // go into the two species streams, each stream word is filtered against
+                    // the cutoff into a bitmask (as the list build does against rc + skin),
+                    // band candidates are decided by the exact rule, then the forces of the
+                    // set bits are added (the species of j is that of the stream)
+                    StreamRings& SR = *SRp;
+                    const float4 fc = warp_frame(warp_box(me, act), keep_reach(s.pt.rc2hi, 0),
+                                                 keep_reach(s.pt.rc2hi, 1), SR, lane);
+                    const float mx = act ? me.x - fc.x : 0.f, my = act ? me.y - fc.y : 0.f,
+                                mz = act ? me.z - fc.z : 0.f;
+                    const float m2x = -2.f * mx, m2y = -2.f * my, m2z = -2.f * mz;
+                    const float mm = act ? fmaf(mz, mz, fmaf(my, my, mx * mx)) : far;
+                    int fill[2] = {0, 0}, done[2] = {0, 0}, cself = -1;
+                    // bitmask of the entries of stream S's word at cq inside the cutoff
+                    auto filter_word = [&](int S, int cq) -> unsigned {
+                        const float4* const rp = SR.rec[S] + (cq & (kSRing - 1));
+                        const float cS = mm - s.pt.rc2lo[si * 2 + S];
+                        unsigned inw = 0u;
+                        float near = far;
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) {
+                            const float d = stream_d(rp[u], m2x, m2y, m2z, cS);
+                            inw = __funnelshift_l(__float_as_uint(d), inw, 1);
+                            near = fminf(near, fabsf(d));
+                        }
+                        const int nv = fill[S] - cq;
+                        unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
+                        if (S == si && cself >= cq && cself < cq + 32)
+                            valid &= ~(0x80000000u >> (cself - cq));
+                        if (!act) valid = 0u;
+                        inw &= valid;
+                        const float bS = s.pt.rc2hi[si * 2 + S] - s.pt.rc2lo[si * 2 + S];
+                        const bool chk = near < bS && valid != 0u;
+                        if (__any_sync(FULL, chk) && chk) {
+                            unsigned bw = valid;
+                            while (bw) {
+                                const int u = __clz(bw);
+                                bw &= 0x7fffffffu >> u;
+                                if (!(fabsf(stream_d(rp[u], m2x, m2y, m2z, cS)) < bS)) continue;
+                                const unsigned bit = 0x80000000u >> u;
+                                inw &= ~bit;
+                                const float4 r = rp[u];
+                                if (!min_image_copy(s, fmaf(m2x, 0.5f, r.x), fmaf(m2y, 0.5f, r.y),
+                                                    fmaf(m2z, 0.5f, r.z)))
+                                    continue;
+                                const int t = (int)SR.idx[S][(cq + u) & (kSRing - 1)];
+                                const int64_t gj = staged_global(Rc, t);
+                                if (r2_exact(s, gi, gj) < s.pt.rc2[si * 2 + S]) inw |= bit;
+                            }
+                        }
+                        return inw;
+                    };
+                    // the forces of the set bits of stream S's word at cq
+                    auto force_word = [&](int S, int cq) {
+                        unsigned inw = filter_word(S, cq);
+                        const float4* const rp = SR.rec[S] + (cq & (kSRing - 1));
+                        // the constants of the species pair (s_i, S)
+                        const int k = si * 2 + S;
+                        const float sig2 = s.pt.sig2[k], e48 = s.pt.eps48[k];
+                        const float fcut = FSHIFT ? s.pt.fcut[k] : 0.f;
+                        const float cpot = s.pt.potential == BBMD_POT_LJ ? 0.5f : 0.0f;
+                        while (inw) {
+                            const int u = __clz(inw);
+                            inw &= 0x7fffffffu >> u;
+                            const float4 r = rp[u];
+                            // p' - m' (0.5 m2 = -m' exactly)
+                            const float dx = fmaf(m2x, 0.5f, r.x), dy = fmaf(m2y, 0.5f, r.y),
+                                        dz = fmaf(m2z, 0.5f, r.z);
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            pair_add_c<FSHIFT>(sig2, e48, cpot, fcut, dx, dy, dz, r2, a);
+                        }
+                    };
+                    auto flush_full = [&](int S) {
+                        if (fill[S] - done[S] >= 32) {
+                            force_word(S, done[S]);
+                            done[S] += 32;
+                            __syncwarp();
+                        }
+                    };
+                    auto flush_last = [&](int S) {
+                        if (fill[S] > done[S]) {
+                            stream_pad(SR, S, fill[S], lane, s.smax);
+                            __syncwarp();
+                            force_word(S, done[S]);
+                            done[S] += 32;
+                            __syncwarp();
+                        }
+                    };
                     StencilScan sc = {-1, 0, 0};
                     bool more = scan_next(Rc, wc, sc);
-                    while (more || done < fill) {
-                        while (more && fill - done < 32 * kRingWords) {
-                            compact_group(sm, sc.g0, sc.re, bx, keepA, keepB, ring, fill, self, cself,
-                                          lane);
-                            sc.g0 += 32;
-                            more = scan_next(Rc, wc, sc);
-                            if (!more) ring_pad(ring, fill, lane, (uint32_t)s.smax);
-                        }
+                    while (more) {
+                        compact_streams(sm, sc.g0, sc.re, SR, fill, self, cself, lane);
+                        sc.g0 += 32;
+                        more = scan_next(Rc, wc, sc);
                         __syncwarp();
-                        const int nw = min(kRingWords, (fill - done + 31) >> 5);
-                        // bitmask of the candidates of ring word cq (a multiple of 32)
-                        // inside the cutoff
-                        auto filter_word = [&](int cq) -> unsigned {
-                            const uint4* ip = reinterpret_cast<const uint4*>(ring + (cq & (kRing - 1)));
-                            unsigned inw = 0u;
-                            float near = far;
-#pragma unroll
-                            for (int v = 0; v < 8; ++v) {
-                                const uint4 iv = ip[v];
-                                const uint32_t ix[4] = {iv.x, iv.y, iv.z, iv.w};
-#pragma unroll
-                                for (int h = 0; h < 4; ++h) {
-                                    const float4 p = sm[ix[h]];
-                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                    const float dlo =
-                                        fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, drc, rcA))));
-                                    inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
-                                    near = fminf(near, fabsf(dlo));
-                                }
-                            }
-                            const int nv = fill - cq;
-                            unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
-                            if (cself >= cq && cself < cq + 32) valid &= ~(0x80000000u >> (cself - cq));
-                            if (!act) valid = 0u;
-                            inw &= valid;
-                            const bool chk = near < bandc && valid != 0u;
-                            if (__any_sync(FULL, chk) && chk) {
-                                unsigned bw = valid;
-                                while (bw) {
-                                    const int u = __clz(bw);
-                                    bw &= 0x7fffffffu >> u;
-                                    const int t = (int)ring[(cq + u) & (kRing - 1)];
-                                    const float4 p = sm[t];
-                                    const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                    const float dlo =
-                                        fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, drc, rcA))));
-                                    if (!(fabsf(dlo) < bandc)) continue;
-                                    const unsigned bit = 0x80000000u >> u;
-                                    inw &= ~bit;
-                                    if (!min_image_copy(s, dx, dy, dz)) continue;
-                                    const int tj = p.w != 0.f ? 1 : 0;
-                                    const int64_t gj = staged_global(Rc, t);
-                                    if (r2_exact(s, gi, gj) < s.pt.rc2[si * 2 + tj]) inw |= bit;
-                                }
-                            }
-                            return inw;
-                        };
-#if BBMD_CELL_PAIRWORDS
-                        // the forces of two words' set bits in one loop: the warp runs to the
-                        // largest count of the pair rather than to each word's largest; a
-                        // flush's words lie in one half of the ring, so the two words' 64
-                        // entries are contiguous
-                        for (int q = 0; q < nw; q += 2) {
-                            const int cq = done + 32 * q;
-                            const unsigned w0 = filter_word(cq);
-                            const unsigned w1 = q + 1 < nw ? filter_word(cq + 32) : 0u;
-                            unsigned long long bits = ((unsigned long long)w0 << 32) | w1;
-                            const uint32_t* const rw = ring + (cq & (kRing - 1));
-                            while (bits) {
-                                const int u = __clzll(bits);
-                                bits &= 0x7fffffffffffffffull >> u;
-                                const float4 p = sm[rw[u]];
-                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                pair_add<FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
-                            }
-                        }
-#else
-                        for (int q = 0; q < nw; ++q) {
-                            const int cq = done + 32 * q;
-                            unsigned inw = filter_word(cq);
-                            while (inw) {
-                                const int u = __clz(inw);
-                                inw &= 0x7fffffffu >> u;
-                                const float4 p = sm[ring[(cq + u) & (kRing - 1)]];
-                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                pair_add<FSHIFT>(T, p.w != 0.f, dx, dy, dz, r2, true, a);
-                            }
-                        }
-#endif
-                        done += 32 * nw;
-                        __syncwarp();
+                        flush_full(0);
+                        flush_full(1);
                     }
+                    flush_last(0);
+                    flush_last(1);
                 }
                 float fx = -a.fx, fy = -a.fy, fz = -a.fz;
                 if (act) {
@@ -970,7 +1047,7 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int lcap = s.lcap8 * 8;
     const int lcap2 = lcap >> 1;  // pair slots per particle
-    uint32_t* const ring = warp_ring(w);
+    StreamRings& SR = warp_streams(w);
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStageBuffers; ++k) mbar_init(&mbar[k], 1);
         ss.next_cell[0] = ss.next_cell[1] = 0;
@@ -998,12 +1075,6 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                 const int self = self0 + li;
                 float4 me = act ? sm[self] : make_float4(-far, -far, -far, 0.f);
                 const int si = me.w != 0.f ? 1 : 0;
-                // threshold as a function of the candidate's species w (0 or 1): R2lo(w); a
-                // band width that covers both species (a wider band only means more exact
-                // tests)
-                const float RloA = s.pt.R2lo[si * 2], dRlo = s.pt.R2lo[si * 2 + 1] - RloA;
-                const float band = fmaxf(s.pt.R2hi[si * 2] - s.pt.R2lo[si * 2],
-                                         s.pt.R2hi[si * 2 + 1] - s.pt.R2lo[si * 2 + 1]);
                 int len = 0;
                 unsigned pend = 0u;
                 // pair slot wi (entries 2 wi, 2 wi + 1) of this particle:
@@ -1017,108 +1088,119 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
                     ++wp;
                     if ((wp & 3) == 0) rowp += rowstep;
                 };
-                const WarpBox bx = warp_box(me, act);
-                const float keepA = keep_reach(s.pt.R2hi, 0), keepB = keep_reach(s.pt.R2hi, 1);
-                int fill = 0, done = 0, cself = -1;
+                const float4 fc = warp_frame(warp_box(me, act), keep_reach(s.pt.R2hi, 0),
+                                             keep_reach(s.pt.R2hi, 1), SR, lane);
+                // the lane relative to the box centre, and its constants per stream
+                const float mx = act ? me.x - fc.x : 0.f, my = act ? me.y - fc.y : 0.f,
+                            mz = act ? me.z - fc.z : 0.f;
+                const float m2x = -2.f * mx, m2y = -2.f * my, m2z = -2.f * mz;
+                const float mm = act ? fmaf(mz, mz, fmaf(my, my, mx * mx)) : far;
+                int fill[2] = {0, 0}, done[2] = {0, 0}, cself = -1;
+                // bitmask of the entries of stream S's word at cq (a multiple of 32) that
+                // enter this particle's list (entry u in bit 31 - u)
+                auto test_word = [&](int S, int cq) -> unsigned {
+                    const float4* const rp = SR.rec[S] + (cq & (kSRing - 1));
+                    const float cS = mm - s.pt.R2lo[si * 2 + S];
+                    unsigned inw = 0u;
+                    float near = far;
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const float d = stream_d(rp[u], m2x, m2y, m2z, cS);
+                        inw = __funnelshift_l(__float_as_uint(d), inw, 1);
+                        near = fminf(near, fabsf(d));
+                    }
+                    const int nv = fill[S] - cq;
+                    unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
+                    if (S == si && cself >= cq && cself < cq + 32)
+                        valid &= ~(0x80000000u >> (cself - cq));
+                    if (!act) valid = 0u;
+                    inw &= valid;
+                    const float bS = s.pt.R2hi[si * 2 + S] - s.pt.R2lo[si * 2 + S];
+                    const bool chk = near < bS && valid != 0u;
+                    if (__any_sync(FULL, chk) && chk) {
+                        // the same FP32 value decides which entries are in the band; those
+                        // are decided by the exact rule
+                        unsigned bw = valid;
+                        while (bw) {
+                            const int u = __clz(bw);
+                            bw &= 0x7fffffffu >> u;
+                            if (!(fabsf(stream_d(rp[u], m2x, m2y, m2z, cS)) < bS)) continue;
+                            const unsigned bit = 0x80000000u >> u;
+                            inw &= ~bit;
+                            // (p' - m' is the separation up to FP32 rounding: enough to tell
+                            // the minimum-image copy from one a box length away)
+                            const float4 r = rp[u];
+                            if (!min_image_copy(s, fmaf(m2x, 0.5f, r.x), fmaf(m2y, 0.5f, r.y),
+                                                fmaf(m2z, 0.5f, r.z)))
+                                continue;
+                            const int t = (int)SR.idx[S][(cq + u) & (kSRing - 1)];
+                            const int64_t gj = staged_global(Rc, t);
+                            if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + S]) inw |= bit;
+                        }
+                    }
+                    return inw;
+                };
+                // the set bits of stream S's word at cq as list entries, in stream order
+                auto append_word = [&](int S, int cq, unsigned bits) {
+                    // the word's 32 entries are contiguous (word starts are multiples of 32
+                    // in a ring of 64)
+                    const uint16_t* const rw = SR.idx[S] + (cq & (kSRing - 1));
+                    // entries go out in pairs (one 32-bit store each at the running row
+                    // pointer; entries beyond the capacity are counted, not stored): a
+                    // pending odd entry is completed by the word's first bit, then two
+                    // bits per iteration; an odd last bit stays pending
+                    if ((len & 1) && bits) {
+                        const int u = __clz(bits);
+                        bits &= 0x7fffffffu >> u;
+                        put_pair(pend | ((unsigned)rw[u] << 16));
+                        ++len;
+                    }
+                    while (bits) {
+                        const int u1 = __clz(bits);
+                        bits &= 0x7fffffffu >> u1;
+                        const unsigned t1 = rw[u1];
+                        if (!bits) {
+                            pend = t1;
+                            ++len;
+                            break;
+                        }
+                        const int u2 = __clz(bits);
+                        bits &= 0x7fffffffu >> u2;
+                        put_pair(t1 | ((unsigned)rw[u2] << 16));
+                        len += 2;
+                    }
+                };
+                // a stream's word is tested and appended as soon as it is full (fewer than
+                // 32 entries wait in each ring before a group adds at most 32)
+                auto flush_full = [&](int S) {
+                    if (fill[S] - done[S] >= 32) {
+                        append_word(S, done[S], test_word(S, done[S]));
+                        done[S] += 32;
+                        __syncwarp();
+                    }
+                };
                 StencilScan sc = {-1, 0, 0};
                 bool more = scan_next(Rc, wc, sc);
-                while (more || done < fill) {
-                    while (more && fill - done < 32 * kRingWords) {
-                        compact_group(sm, sc.g0, sc.re, bx, keepA, keepB, ring, fill, self, cself, lane);
-                        sc.g0 += 32;
-                        more = scan_next(Rc, wc, sc);
-                        if (!more) ring_pad(ring, fill, lane, (uint32_t)s.smax);
-                    }
+                while (more) {
+                    compact_streams(sm, sc.g0, sc.re, SR, fill, self, cself, lane);
+                    sc.g0 += 32;
+                    more = scan_next(Rc, wc, sc);
                     __syncwarp();
-                    const int nw = min(kRingWords, (fill - done + 31) >> 5);
-                    // bitmask of the candidates of ring word cq (stream position, a
-                    // multiple of 32) that enter this particle's list
-                    auto test_word = [&](int cq) -> unsigned {
-                        unsigned inw = 0u;
-                        const uint4* ip = reinterpret_cast<const uint4*>(ring + (cq & (kRing - 1)));
-                        float near = far;
-#pragma unroll
-                        for (int v = 0; v < 8; ++v) {
-                            const uint4 iv = ip[v];
-                            const uint32_t ix[4] = {iv.x, iv.y, iv.z, iv.w};
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                const float4 p = sm[ix[h]];
-                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                // r^2 - R2lo(species of j), one FMA chain; sign = inside
-                                const float dlo = fmaf(dz, dz,
-                                                       fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
-                                inw = __funnelshift_l(__float_as_uint(dlo), inw, 1);
-                                near = fminf(near, fabsf(dlo));
-                            }
-                        }
-                        const int nv = fill - cq;
-                        unsigned valid = nv >= 32 ? 0xffffffffu : ~(0xffffffffu >> nv);
-                        if (cself >= cq && cself < cq + 32) valid &= ~(0x80000000u >> (cself - cq));
-                        if (!act) valid = 0u;
-                        inw &= valid;
-                        const bool chk = near < band && valid != 0u;
-                        if (__any_sync(FULL, chk) && chk) {
-                            // the same FP32 value decides which candidates are in the band;
-                            // those are decided by the exact rule
-                            unsigned bw = valid;
-                            while (bw) {
-                                const int u = __clz(bw);
-                                bw &= 0x7fffffffu >> u;
-                                const int t = (int)ring[(cq + u) & (kRing - 1)];
-                                const float4 p = sm[t];
-                                const float dx = p.x - me.x, dy = p.y - me.y, dz = p.z - me.z;
-                                const float dlo = fmaf(dz, dz,
-                                                       fmaf(dy, dy, fmaf(dx, dx, -fmaf(p.w, dRlo, RloA))));
-                                if (!(fabsf(dlo) < band)) continue;
-                                const unsigned bit = 0x80000000u >> u;
-                                inw &= ~bit;
-                                if (!min_image_copy(s, dx, dy, dz)) continue;
-                                const int tj = p.w != 0.f ? 1 : 0;
-                                const int64_t gj = staged_global(Rc, t);
-                                if (r2_exact(s, gi, gj) < s.pt.R2[si * 2 + tj]) inw |= bit;
-                            }
-                        }
-                        return inw;
-                    };
-                    // the set bits of word cq as list entries, in candidate order
-                    auto append_word = [&](int cq, unsigned bits) {
-                        // the word's 32 ring entries are contiguous (word starts are
-                        // multiples of 32 in a ring of 256)
-                        const uint32_t* const rw = ring + (cq & (kRing - 1));
-                        // entries go out in pairs (one 32-bit store each at the running row
-                        // pointer; entries beyond the capacity are counted, not stored): a
-                        // pending odd entry is completed by the word's first bit, then two
-                        // bits per iteration; an odd last bit stays pending
-                        if ((len & 1) && bits) {
-                            const int u = __clz(bits);
-                            bits &= 0x7fffffffu >> u;
-                            put_pair(pend | (rw[u] << 16));
-                            ++len;
-                        }
-                        while (bits) {
-                            const int u1 = __clz(bits);
-                            bits &= 0x7fffffffu >> u1;
-                            const unsigned t1 = rw[u1];
-                            if (!bits) {
-                                pend = t1;
-                                ++len;
-                                break;
-                            }
-                            const int u2 = __clz(bits);
-                            bits &= 0x7fffffffu >> u2;
-                            put_pair(t1 | (rw[u2] << 16));
-                            len += 2;
-                        }
-                    };
-                    // one word at a time, the loop kept rolled: testing all words before
-                    // appending, unrolled, made a kernel large enough to stall on
-                    // instruction fetch (6-11 % slower)
-#pragma unroll 1
-                    for (int q = 0; q < nw; ++q) append_word(done + 32 * q, test_word(done + 32 * q));
-                    done += 32 * nw;
-                    __syncwarp();
+                    flush_full(0);
+                    flush_full(1);
                 }
+                // the partial last word of each stream
+                auto flush_last = [&](int S) {
+                    if (fill[S] > done[S]) {
+                        stream_pad(SR, S, fill[S], lane, s.smax);
+                        __syncwarp();
+                        append_word(S, done[S], test_word(S, done[S]));
+                        done[S] += 32;
+                        __syncwarp();
+                    }
+                };
+                flush_last(0);
+                flush_last(1);
                 if (len > lcap) {
                     // the list is cut: flagged for the host (which grows the capacity at its
                     // next synchronising call) and, until then, the forces come from the
@@ -1194,8 +1276,8 @@ __device__ __forceinline__ void run_phase(int phase, const DevSim& s, int lb, in
         case kPhForce:
             // the list body, or for a replica whose lists are cut (and in cell mode) the
             // stencil body: each returns at once when not selected
-            force_body<0, KE, FSHIFT>(s, lb, lg);
-            force_body<1, KE, FSHIFT>(s, lb, lg);
+            force_body<0, KE, FSHIFT, false>(s, lb, lg);
+            force_body<1, KE, FSHIFT, false>(s, lb, lg);
             break;
         default: finalize_body(s, KE ? 1 : 0); break;
     }

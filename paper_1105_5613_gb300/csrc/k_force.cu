@@ -76,6 +76,12 @@ static_assert(kRegion <= kBW * 32, "one thread per staged region cell");
 #define BBMD_LIST_AHEAD 2
 #endif
 constexpr int kListAhead = BBMD_LIST_AHEAD;  // list rows in flight ahead of the pair loop
+#ifndef BBMD_LIST_PREFETCH
+#define BBMD_LIST_PREFETCH 4
+#endif
+// list rows prefetched into L2 this many rows ahead of the pair loop (0: none), so that
+// the register loads two rows ahead find them in L2 rather than in DRAM
+constexpr int kListPrefetch = BBMD_LIST_PREFETCH;
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -871,6 +877,8 @@ __device__ __forceinline__ void force_body(const DevSim& s, int lb, int lg) {
                         } else {
                             e1 = kb + 2 < myrows ? __ldcs(lp + (int64_t)(kb + 2) * s.npad) : sent;
                         }
+                        if (kListPrefetch > 0 && kb + kListPrefetch < myrows)
+                            prefetch_l2(lp + (int64_t)(kb + kListPrefetch) * s.npad);
                         float near = far;
                         pair_fast<FSHIFT>(T, me, sm[lo16(e.x)], a, near);
                         pair_fast<FSHIFT>(T, me, sm[hi16(e.x)], a, near);

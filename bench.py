@@ -259,7 +259,11 @@ def run_ours(args):
 
         ms = max_over_ranks(ms, "cuda")
     obs = sim.observe(bbmd.OBS_ENERGY)
-    block_z = sim.info()["block_z"]
+    info = sim.info()
+    block_z = info["block_z"]
+    # the re-tuning's per-shape times on the equilibrated liquid (0: shape not timed)
+    shape_times = {"block_z": [1, 2, 4, 8], "force_ms": info["shape_force_ms"],
+                   "list_ms": info["shape_list_ms"]}
     clocks = clk.summary()
 
     # ---- measured FP32 / FP64 FMA peaks of this GPU (the ALU roofline denominators) ----
@@ -399,6 +403,7 @@ def run_ours(args):
         "fma_probe": probe,
         "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
         "block_z": block_z,
+        "shape_times": shape_times,
         "rebuilds_per_step": nreb / nprof,
         # per step: integrate, 2 trigger kernels, 9 gated sort kernels, gated list build,
         # list force and the stencil force that stands in for cut lists (one of the two

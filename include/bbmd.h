@@ -87,8 +87,10 @@ enum { BBMD_THERMO_NVE = 0, BBMD_THERMO_NH = 1 };
  * stencil_capacity: maximum particles staged for one block of cells, i.e. in the
  *   4 x 4 x (block_z + 2) cells around it (0 = from the density, with 15 % headroom).
  * block_z: block shape of the force and list kernels, 2 x 2 x block_z cells per CTA:
- *   0 = chosen at creation by timing every shape that fits (1, 2, 4, 8) on the initial
- *   state; 1, 2, 4 or 8 = that shape.
+ *   0 = chosen at creation by timing every shape that fits on the initial state (1, 2, 4
+ *   and 8 in the FP64 form; 1, 2 and 4 in mixed precision, whose FP32 coordinates
+ *   relative to the block's middle reach 5 cells with 8, where their rounding puts the
+ *   largest force errors of a large liquid near the 1e-4 bar); 1, 2, 4 or 8 = that shape.
  * init_jitter: with pos == NULL (device-generated FCC lattice), coordinate d of site i is
  *   moved by init_jitter * (2u - 1), u = uniform01(draw 3i + d of stream 5) under the
  *   creation seed (0 = the perfect lattice); the displaced position is quantised and

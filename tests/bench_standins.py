@@ -68,7 +68,8 @@ class StandinSim:
         return {q: 0.1 * nsteps for q in bbmd.PHASES}, 1
 
     def info(self):
-        return {"block_z": 4, "device_bytes": 123 * self.n}
+        return {"block_z": 4, "device_bytes": 123 * self.n, "shape_force_ms": [0.4, 0.3, 0.2, 0.0],
+                "shape_list_ms": [1.0, 0.9, 0.8, 0.0]}
 
     def observe(self, mask, nbins=500, rmax=5.0, k=7.25):
         return {"temperature": 1.0, "pe": -5.0 * self.n, "ke": 1.5 * self.n, "xi": 0.0,

@@ -95,6 +95,22 @@ def test_forces_mixed(pot, shift, rc_all, mode):
     sim.close()
 
 
+def test_forces_liquid_37k_every_particle():
+    # every particle of a 37 044-particle liquid (melted for 40 steps from a shaken
+    # lattice) against the oracle, in the shape the autotuner picks for it (mixed
+    # precision picks among 2 x 2 x 1, 2 and 4: see bbmd.h)
+    sim, n, L, pos, vel, sp, p = make(ncell=21, shake=0.12)
+    assert sim.info()["block_z"] in (1, 2, 4)
+    sim.step(40, 0.005)
+    gp, _, _ = sim.get_state()
+    xq, _, _ = quantized(gp, L)
+    Fo = oracle.forces(xq, sp, L, oracle_params(p))[0]
+    e = force_errors(sim.get_forces(), Fo)
+    assert sim.observe(0)["n_rebuilds"] > 1
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+    sim.close()
+
+
 @pytest.mark.parametrize("ncell", [8, 10])
 @pytest.mark.parametrize("pot,shift,rc_all", [(0, 1, None), (0, 2, None), (1, 2, None),
                                              (1, 2, 1.2)])

@@ -86,11 +86,13 @@ def test_autotuner_picks_a_timed_shape():
     p = bbmd.ka_params()
     sim = bbmd.Sim(p, n, L, sp, pos, vel)
     info = sim.info()
-    assert info["block_z"] in SHAPES
+    # mixed precision times 2 x 2 x 1, 2 and 4 (8 only on request: bbmd.h)
+    assert info["block_z"] in (1, 2, 4)
     k = SHAPES.index(info["block_z"])
-    assert all(t > 0 for t in info["shape_force_ms"])
-    assert all(t > 0 for t in info["shape_list_ms"])
-    cost = [f + 0.25 * l for f, l in zip(info["shape_force_ms"], info["shape_list_ms"])]
+    assert all(t > 0 for t in info["shape_force_ms"][:3])
+    assert all(t > 0 for t in info["shape_list_ms"][:3])
+    assert info["shape_force_ms"][3] == 0.0 and info["shape_list_ms"][3] == 0.0
+    cost = [f + 0.25 * l for f, l in zip(info["shape_force_ms"][:3], info["shape_list_ms"][:3])]
     assert cost[k] <= min(cost) * (1 + 1e-6)
     xq, xfix, kx = quantized(pos, L)
     Fo = oracle.forces(xq, sp, L, oracle_params(p), "cells")[0]

@@ -84,13 +84,13 @@ enum { BBMD_THERMO_NVE = 0, BBMD_THERMO_NH = 1 };
  *   (creation, observe, get_state, set_state, get_forces, get_neighbors, ...) grows the
  *   capacity to the longest list plus an eighth and rebuilds the lists.  Only a list
  *   longer than 4096 entries is reported, as BBMD_ERR_LIST_OVERFLOW.
- * stencil_capacity: maximum particles staged for one block of cells, i.e. in the
- *   4 x 4 x (block_z + 2) cells around it (0 = from the density, with 15 % headroom).
- * block_z: block shape of the force and list kernels, 2 x 2 x block_z cells per CTA:
- *   0 = chosen at creation by timing every shape that fits on the initial state (1, 2, 4
- *   and 8 in the FP64 form; 1, 2 and 4 in mixed precision, whose FP32 coordinates
- *   relative to the block's middle reach 5 cells with 8, where their rounding puts the
- *   largest force errors of a large liquid near the 1e-4 bar); 1, 2, 4 or 8 = that shape.
+ * stencil_capacity: maximum particles staged for one block of cells, i.e. in the cells
+ *   around it (one layer on every side; 0 = from the density, with 15 % headroom).
+ * block_z: block shape code of the force and list kernels, one CTA per block at a time:
+ *   1, 2 or 4 = blocks of 2 x 2 x block_z cells; 8 = blocks of 4 x 4 x 2 cells (32 cells);
+ *   0 = chosen at creation by timing every shape that fits on the initial state.  (Every
+ *   shape keeps its cells within 2 cells of the block's middle, so the FP32 coordinates of
+ *   mixed precision stay within 3 cells of their frame.)
  * init_jitter: with pos == NULL (device-generated FCC lattice), coordinate d of site i is
  *   moved by init_jitter * (2u - 1), u = uniform01(draw 3i + d of stream 5) under the
  *   creation seed (0 = the perfect lattice); the displaced position is quantised and
@@ -180,7 +180,7 @@ typedef struct {
     int32_t list_capacity;
     int32_t stencil_capacity;
     int64_t device_bytes;    /* device memory held by the handle           */
-    int32_t block_z;         /* block shape in use (2 x 2 x block_z cells) */
+    int32_t block_z;         /* block shape code in use (see bbmd_params)  */
     float shape_force_ms[4]; /* autotuner: force / list-build ms per launch   */
     float shape_list_ms[4];  /*   for block_z = 1, 2, 4, 8, measured on a     */
                              /*   part of the box and scaled to all of it     */

@@ -264,7 +264,9 @@ void apply_shape(bbmd_sim* sim, int bz) {
     D.block_z = bz;
     D.region_cells = region_cells_of(bz);
     D.smax = shape_smax(sim, bz);
-    D.nblocks = (int64_t)((D.nc[0] + 1) / 2) * ((D.nc[1] + 1) / 2) * ((D.nc[2] + bz - 1) / bz);
+    const int bxy = block_xy_of(bz), bzc = block_zc_of(bz);
+    D.nblocks = (int64_t)((D.nc[0] + bxy - 1) / bxy) * ((D.nc[1] + bxy - 1) / bxy) *
+                ((D.nc[2] + bzc - 1) / bzc);
     int64_t g = (int64_t)sim->nsm * force_blocks_per_sm(D);
     if (g > D.nblocks) g = D.nblocks;
     if (g > kMaxPartials) g = kMaxPartials;
@@ -371,7 +373,7 @@ bbmd_status autotune_shape(bbmd_sim* sim, float rebuild_rate = 0.25f) {
         apply_shape(sim, bz);
         // the timed launches cover the first nb blocks only
         DevSim Dt = D;
-        const int64_t cpb = 4 * (int64_t)bz;
+        const int64_t cpb = block_cells_of(bz);
         Dt.nblocks = std::min<int64_t>(D.nblocks, (target_cells + cpb - 1) / cpb);
         Dt.grid_cell = (int32_t)std::min<int64_t>(Dt.grid_cell, Dt.nblocks);
         Dt.grid_list = (int32_t)std::min<int64_t>(Dt.grid_list, Dt.nblocks);
@@ -578,19 +580,16 @@ bbmd_status bbmd_create(const bbmd_params* params, int64_t n, const double box[3
     // params->block_z fixes one)
     for (int bz : kShapes) {
         if (params->block_z != 0 && bz != params->block_z) continue;
-        // mixed precision stages FP32 coordinates relative to the block's middle: with
-        // Z = 8 they reach 5 cells from it (14 at the benchmark density), where FP32
-        // rounding put the largest force error of a 37 000-particle liquid at 1.01e-4, above
-        // the 1e-4 bar; Z = 4 (3 cells) held 8e-5.  Z = 8 is used in mixed precision only
-        // when asked for.
-        if (params->block_z == 0 && params->precision == BBMD_PREC_MIXED && bz == 8) continue;
-        if (bz > D.nc[2]) continue;  // the staged region may wrap the box at most once
+        // a block's own cells are distinct cells of the box (the staged region wraps the
+        // box at most once)
+        if (block_xy_of(bz) > D.nc[0] || block_xy_of(bz) > D.nc[1] || block_zc_of(bz) > D.nc[2])
+            continue;
         if (!shape_fits(sim, bz)) continue;
         sim->shapes.push_back(bz);
     }
     if (sim->shapes.empty()) {
         std::fprintf(stderr, "bbmd_create: no block shape fits (staged region beyond shared "
-                             "memory, or block_z larger than the cells along z)\n");
+                             "memory, or the block larger than the cells along an axis)\n");
         bbmd_destroy(sim);
         return BBMD_ERR_ARG;
     }

@@ -10,7 +10,7 @@
 //   F[npad]      float4  mixed-precision force (w = per-particle energy on energy passes)
 //   Fd[3][npad]  double  FP64-form force
 //   list[lcap8][npad][8] uint16  Verlet list: offsets into the staged region (the cells
-//                                 around the particle's block of 2 x 2 x block_z cells)
+//                                 around the particle's block of cells)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,11 +20,21 @@
 namespace bbmd {
 
 constexpr int kVelExp = 52;            // velocity unit 2^-52
-// Block shapes of the force / list kernels: blocks of 2 x 2 x Z cells, one CTA per block
-// at a time, the 4 x 4 x (Z + 2) cells around it staged in shared memory.  k_force.cu is
-// compiled once per shape (namespace z<Z>); a handle runs the shape chosen at creation.
+// Block shapes of the force / list kernels, by code bz: 1, 2 and 4 are blocks of 2 x 2 x bz
+// cells, 8 is a block of 4 x 4 x 2 cells (32 cells, like 2 x 2 x 8, but its cells are at
+// most 2 cells from the block's middle along every axis).  One CTA works on a block at a
+// time, with the (X + 2) x (Y + 2) x (Z + 2) cells around it staged in shared memory.
+// k_force.cu is compiled once per shape (namespace z<bz>); a handle runs the shape chosen
+// at creation.
 constexpr int kShapes[4] = {1, 2, 4, 8};
-__host__ __device__ constexpr int region_cells_of(int bz) { return 16 * (bz + 2); }
+__host__ __device__ constexpr int block_xy_of(int bz) { return bz == 8 ? 4 : 2; }
+__host__ __device__ constexpr int block_zc_of(int bz) { return bz == 8 ? 2 : bz; }
+__host__ __device__ constexpr int block_cells_of(int bz) {
+    return block_xy_of(bz) * block_xy_of(bz) * block_zc_of(bz);
+}
+__host__ __device__ constexpr int region_cells_of(int bz) {
+    return (block_xy_of(bz) + 2) * (block_xy_of(bz) + 2) * (block_zc_of(bz) + 2);
+}
 constexpr int kMaxPartials = 8192;     // per-block FP64 partial sums
 constexpr float kBand = 1e-5f;         // relative band around a threshold for the FP64 re-test
 
@@ -83,9 +93,9 @@ struct alignas(16) DevSim {
     float sx;                // 2^-k
     double sxd;
     int32_t lcap8, smax;     // list capacity / 8; staged capacity of one block region
-    int32_t block_z;         // block shape: 2 x 2 x block_z cells (one of kShapes)
+    int32_t block_z;         // block shape code (one of kShapes; block_xy_of, block_zc_of)
     int32_t region_cells;    // cells staged per block: 4 x 4 x (block_z + 2)
-    int64_t nblocks;         // blocks of 2 x 2 x block_z cells
+    int64_t nblocks;         // blocks of the shape (block_xy_of x block_xy_of x block_zc_of)
     float halfL[3];          // L/2 (FP32) per axis
     int32_t nbr_mode, precision;
     float disp2;             // steepest descent: rebuild threshold on |x - x_build|^2

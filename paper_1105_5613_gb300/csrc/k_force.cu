@@ -21,12 +21,13 @@
 // relative band of the cutoff is decided by the exact FP64 rule in a rare fix-up after
 // each batch of 8 pairs, so the interacting set equals the FP64 definition.
 //
-// This file is compiled once per block shape, BBMD_BLOCK_Z = 1, 2, 4 or 8 cells along z,
-// into namespace bbmd::z<BBMD_BLOCK_Z>; the handle picks one shape at creation.
+// This file is compiled once per block shape, code BBMD_BLOCK_Z = 1, 2 or 4 (2 x 2 x Z
+// cells) or 8 (4 x 4 x 2 cells), into namespace bbmd::z<BBMD_BLOCK_Z>; the handle picks one
+// shape at creation.
 #include "bbmd_internal.cuh"
 
 #ifndef BBMD_BLOCK_Z
-#error "k_force.cu is compiled once per block shape: define BBMD_BLOCK_Z (1, 2, 4 or 8)"
+#error "k_force.cu is compiled once per block shape: define BBMD_BLOCK_Z (code 1, 2, 4 or 8)"
 #endif
 // warps per CTA and resident CTAs per SM targeted by the force and list kernels, per shape
 #if BBMD_BLOCK_Z == 1
@@ -67,10 +68,12 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float kFar = 1.0e15f;
-constexpr int kBlockZ = BBMD_BLOCK_Z;
-constexpr int kBW = BBMD_BLOCK_WARPS;              // warps per CTA
-constexpr int kCells = 4 * kBlockZ;                // cells per block (warp w: w, w + kBW, ...)
-constexpr int kRegion = region_cells_of(kBlockZ);  // cells staged per block: 4 x 4 x (Z + 2)
+constexpr int kBlockXY = block_xy_of(BBMD_BLOCK_Z);  // cells of a block along x and y
+constexpr int kBlockZ = block_zc_of(BBMD_BLOCK_Z);   // cells of a block along z
+constexpr int kRXY = kBlockXY + 2;                   // region cells along x and y
+constexpr int kBW = BBMD_BLOCK_WARPS;                // warps per CTA
+constexpr int kCells = block_cells_of(BBMD_BLOCK_Z);   // cells per block
+constexpr int kRegion = region_cells_of(BBMD_BLOCK_Z);  // cells staged per block
 static_assert(kRegion <= kBW * 32, "one thread per staged region cell");
 #ifndef BBMD_LIST_AHEAD
 #define BBMD_LIST_AHEAD 2
@@ -89,7 +92,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// The region of cells staged for one block: 4 x 4 x (Z + 2), index q = (z*4 + y)*4 + x.
+// The region of cells staged for one block: (X + 2) x (Y + 2) x (Z + 2) cells, index
+// q = (z * (Y + 2) + y) * (X + 2) + x.
 struct Region {
     int off[kRegion + 1];      // prefix of staged counts (clamped to smax); off[kRegion] = total
     int start[kRegion];        // first particle of each region cell
@@ -168,10 +172,10 @@ struct BlockPos {
 };
 
 __device__ __forceinline__ BlockPos block_pos(const DevSim& s, int64_t blk) {
-    const int nbx = (s.nc[0] + 1) >> 1, nby = (s.nc[1] + 1) >> 1;
+    const int nbx = (s.nc[0] + kBlockXY - 1) / kBlockXY, nby = (s.nc[1] + kBlockXY - 1) / kBlockXY;
     BlockPos b;
-    b.a0[0] = (int)(blk % nbx) * 2;
-    b.a0[1] = (int)((blk / nbx) % nby) * 2;
+    b.a0[0] = (int)(blk % nbx) * kBlockXY;
+    b.a0[1] = (int)((blk / nbx) % nby) * kBlockXY;
     b.a0[2] = (int)(blk / ((int64_t)nbx * nby)) * kBlockZ;
     return b;
 }
@@ -183,7 +187,7 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
     const int tid = threadIdx.x, lane = tid & 31;
     int cnt = 0;
     if (tid < kRegion) {
-        const int r[3] = {tid & 3, (tid >> 2) & 3, tid >> 4};
+        const int r[3] = {tid % kRXY, (tid / kRXY) % kRXY, tid / (kRXY * kRXY)};
         int a[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -197,9 +201,9 @@ __device__ void region_info(const DevSim& s, const BlockPos& b, Region& R) {
                 wrap = s.Lfix[d];
             }
             a[d] = aa;
-            // block frame: the boundary between the block's cells (x, y) and, along z, the
-            // boundary at the middle of the block (the centre of the cell when Z = 1)
-            const long long fb = d < 2 ? (long long)(b.a0[d] + 1) * s.D[d]
+            // block frame: the cell boundary at the middle of the block (along z, the centre
+            // of the cell when the block is one cell high)
+            const long long fb = d < 2 ? (long long)(b.a0[d] + kBlockXY / 2) * s.D[d]
                                  : kBlockZ == 1 ? frame_axis(b.a0[d], s.D[d])
                                                 : (long long)(b.a0[d] + kBlockZ / 2) * s.D[d];
             const long long fr = frame_axis(aa, s.D[d]) + wrap;
@@ -352,7 +356,7 @@ struct WarpCell {
 
 __device__ __forceinline__ WarpCell warp_cell(const DevSim& s, const BlockPos& b, int w) {
     WarpCell wc;
-    const int o[3] = {w & 1, (w >> 1) & 1, w >> 2};
+    const int o[3] = {w % kBlockXY, (w / kBlockXY) % kBlockXY, w / (kBlockXY * kBlockXY)};
     int a[3];
     wc.valid = true;
 #pragma unroll
@@ -362,7 +366,7 @@ __device__ __forceinline__ WarpCell warp_cell(const DevSim& s, const BlockPos& b
         wc.wr[d] = o[d];
     }
     wc.c = wc.valid ? (a[2] * s.nc[1] + a[1]) * s.nc[0] + a[0] : 0;
-    wc.rq = ((1 + o[2]) * 4 + (1 + o[1])) * 4 + (1 + o[0]);
+    wc.rq = ((1 + o[2]) * kRXY + (1 + o[1])) * kRXY + (1 + o[0]);
     return wc;
 }
 
@@ -454,8 +458,8 @@ __device__ __forceinline__ bool min_image_copy(const DevSim& s, float dx, float 
 // runs for a few pairs per million.  Called out of line (pair_band_call), it keeps the
 // lane's pair constants and accumulators in local memory (a stack frame); inline, it
 // costs registers.  Inline is faster where the list kernel has 128 registers a thread
-// (2 x 2 x 4 and 2 x 2 x 8: 6 % at 2 M particles); out of line where it has fewer
-// (2 x 2 x 1 and 2 x 2 x 2: inline is 20 % slower there), and in the persistent batch
+// (shapes 4 and 8: 6 % at 2 M particles); out of line where it has fewer (2 x 2 x 1 and
+// 2 x 2 x 2: inline is 20 % slower there), and in the persistent batch
 // kernel, whose other phases share the register budget (inline, some of its forms spill).
 #ifndef BBMD_BAND_INLINE
 #define BBMD_BAND_INLINE (BBMD_BLOCK_Z >= 4)
@@ -509,7 +513,7 @@ __device__ __forceinline__ unsigned hi16(unsigned w) { return w >> 16; }
 __device__ __forceinline__ void stencil_run(const Region& R, const WarpCell& wc, int row, int& rs,
                                             int& re) {
     const int ry = wc.wr[1] + row % 3, rz = wc.wr[2] + row / 3;
-    const int q0 = (rz * 4 + ry) * 4 + wc.wr[0];
+    const int q0 = (rz * kRXY + ry) * kRXY + wc.wr[0];
     rs = R.off[q0];
     re = R.off[q0 + 3];
 }

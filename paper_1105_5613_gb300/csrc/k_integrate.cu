@@ -468,10 +468,11 @@ __global__ void __launch_bounds__(kThreads) k_unpack_cells(DevSim s, int64_t* ce
 __device__ int64_t stencil_slot(const DevSim& s, int c, int t) {
     int ax, ay, az;
     cell_coords(c, s.nc, ax, ay, az);
-    const int a0[3] = {ax & ~1, ay & ~1, az - az % s.block_z};
+    const int bxy = block_xy_of(s.block_z), bzc = block_zc_of(s.block_z), rxy = bxy + 2;
+    const int a0[3] = {ax - ax % bxy, ay - ay % bxy, az - az % bzc};
     int acc = 0;
     for (int q = 0; q < s.region_cells; ++q) {
-        const int r[3] = {q & 3, (q >> 2) & 3, q >> 4};
+        const int r[3] = {q % rxy, (q / rxy) % rxy, q / (rxy * rxy)};
         int b[3];
         for (int d = 0; d < 3; ++d) {
             int bb = a0[d] - 1 + r[d];

@@ -95,12 +95,13 @@ def test_forces_mixed(pot, shift, rc_all, mode):
     sim.close()
 
 
-def test_forces_liquid_37k_every_particle():
+@pytest.mark.parametrize("bz", [0, 4, 8])
+def test_forces_liquid_37k_every_particle(bz):
     # every particle of a 37 044-particle liquid (melted for 40 steps from a shaken
-    # lattice) against the oracle, in the shape the autotuner picks for it (mixed
-    # precision picks among 2 x 2 x 1, 2 and 4: see bbmd.h)
-    sim, n, L, pos, vel, sp, p = make(ncell=21, shake=0.12)
-    assert sim.info()["block_z"] in (1, 2, 4)
+    # lattice) against the oracle: in the shape the autotuner picks (0), and in the two
+    # shapes of largest extent (2 x 2 x 4 and 4 x 4 x 2: FP32 coordinates up to 3 cells
+    # from their frame)
+    sim, n, L, pos, vel, sp, p = make(ncell=21, shake=0.12, block_z=bz)
     sim.step(40, 0.005)
     gp, _, _ = sim.get_state()
     xq, _, _ = quantized(gp, L)

@@ -1,8 +1,8 @@
-"""Every block shape of the force and list kernels (2 x 2 x Z cells per CTA, Z = 1, 2, 4, 8)
-against the oracle, and the creation-time autotuner that picks one.
+"""Every block shape of the force and list kernels (codes 1, 2, 4: 2 x 2 x Z cells per CTA;
+8: 4 x 4 x 2 cells) against the oracle, and the creation-time autotuner that picks one.
 
-nc = 8 cells per axis (ncell 16): the 4 x 4 x (Z + 2) staged region wraps the box along z
-for Z = 8; nc = 9 (ncell 18): the last block along z is ragged for Z = 2, 4, 8."""
+nc = 8 cells per axis (ncell 16); nc = 9 (ncell 18): the last block along z is ragged for
+Z = 2 and 4, and along x and y for the 4 x 4 x 2 block."""
 import numpy as np
 import pytest
 
@@ -86,13 +86,11 @@ def test_autotuner_picks_a_timed_shape():
     p = bbmd.ka_params()
     sim = bbmd.Sim(p, n, L, sp, pos, vel)
     info = sim.info()
-    # mixed precision times 2 x 2 x 1, 2 and 4 (8 only on request: bbmd.h)
-    assert info["block_z"] in (1, 2, 4)
+    assert info["block_z"] in SHAPES
     k = SHAPES.index(info["block_z"])
-    assert all(t > 0 for t in info["shape_force_ms"][:3])
-    assert all(t > 0 for t in info["shape_list_ms"][:3])
-    assert info["shape_force_ms"][3] == 0.0 and info["shape_list_ms"][3] == 0.0
-    cost = [f + 0.25 * l for f, l in zip(info["shape_force_ms"][:3], info["shape_list_ms"][:3])]
+    assert all(t > 0 for t in info["shape_force_ms"])
+    assert all(t > 0 for t in info["shape_list_ms"])
+    cost = [f + 0.25 * l for f, l in zip(info["shape_force_ms"], info["shape_list_ms"])]
     assert cost[k] <= min(cost) * (1 + 1e-6)
     xq, xfix, kx = quantized(pos, L)
     Fo = oracle.forces(xq, sp, L, oracle_params(p), "cells")[0]
@@ -102,16 +100,18 @@ def test_autotuner_picks_a_timed_shape():
 
 
 def test_shapes_that_do_not_fit_are_skipped():
-    # nc = 6 along each axis: Z = 8 does not fit, the autotuner times 1, 2, 4 only
-    n, L, pos, vel, sp = mixture(12, shake=0.12)
+    # nc = 3 along each axis: 2 x 2 x 4 and 4 x 4 x 2 do not fit (a block's cells must be
+    # distinct cells of the box), the autotuner times 1 and 2 only
+    n, L, pos, vel, sp = mixture(7, shake=0.12)
     sim = bbmd.Sim(bbmd.ka_params(), n, L, sp, pos, vel)
     info = sim.info()
-    assert info["nc"] == [6, 6, 6]
-    assert info["block_z"] in (1, 2, 4)
-    assert info["shape_force_ms"][3] == 0.0
+    assert info["nc"] == [3, 3, 3]
+    assert info["block_z"] in (1, 2)
+    assert info["shape_force_ms"][2] == 0.0 and info["shape_force_ms"][3] == 0.0
     sim.close()
-    with pytest.raises(bbmd.BBMDError):
-        bbmd.Sim(bbmd.ka_params(block_z=8), n, L, sp, pos, vel)
+    for bz in (4, 8):
+        with pytest.raises(bbmd.BBMDError):
+            bbmd.Sim(bbmd.ka_params(block_z=bz), n, L, sp, pos, vel)
 
 
 def test_tune_on_the_current_state():

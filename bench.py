@@ -1,7 +1,7 @@
 """Benchmark of the hot path: particle-steps/s of the binary Lennard-Jones mixture on one
 GB300, default workload = the 16,384,000-particle supercooling quench (FCC 4*160^3, 80:20,
 rho = 1.2, Nose-Hoover ramp 2.0 -> 0.4 over 1e5 steps, dt = 0.005, mixed precision,
-Verlet list with skin 0.3).
+Verlet list with skin 0.4 by default, --skin).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -53,7 +53,7 @@ def workload_config(args, ws):
     n = 4 * args.ncell ** 3
     return {"workload": f"supercooling quench, N={n} (4*{args.ncell}^3 FCC, 80:20), rho=1.2, "
                         "equilibrated at T=2.0, Nose-Hoover ramp 2.0->0.4 over 1e5 steps, "
-                        "dt=0.005, mixed, Verlet skin 0.3",
+                        f"dt=0.005, mixed, Verlet skin {args.skin}",
             "equilibration_steps": args.equil, "n_particles": n, "box": gen.box_for(n, 1.2),
             "parallelism": f"replicas x{ws}",
             "l2": "state and per-step traffic (>6 GB) far larger than the 129 MB L2"}
@@ -199,7 +199,7 @@ def run_ours(args):
     sp = gen.assign_species(n, n // 5, 0)
     stream = make_stream()
     p = bbmd.ka_params(nbr_mode=bbmd.NBR_CELL if args.profile_cell else bbmd.NBR_VERLET,
-                       block_z=args.block_z)
+                       block_z=args.block_z, skin=args.skin)
     sim = bbmd.Sim(p, n, L, sp, None, None, T0=T_HIGH, seed=rank, stream=stream.cuda_stream,
                    use_torch_allocator=True)
     step = 0
@@ -307,7 +307,7 @@ def run_ours(args):
 
     # ---- FP64 form on the same workload (a few steps) ----
     def leg_fp64():
-        p64 = bbmd.ka_params(precision=bbmd.PREC_FP64)
+        p64 = bbmd.ka_params(precision=bbmd.PREC_FP64, skin=args.skin)
         sim64 = bbmd.Sim(p64, n, L, sp, None, None, T0=T_HIGH, seed=rank,
                          stream=stream.cuda_stream, use_torch_allocator=True)
         sim64.step(1, DT, therm(1))
@@ -329,7 +329,7 @@ def run_ours(args):
     # ---- soft-sphere mixture with the shifted-force truncation (Eqs. sc0, mod0), the paper's
     # own benchmark potential, on the same N: melted at T=2.0, then timed at T=0.5 ----
     def leg_soft():
-        ps = bbmd.ka_params(potential=bbmd.POT_SOFT, shift=bbmd.SHIFT_FORCE)
+        ps = bbmd.ka_params(potential=bbmd.POT_SOFT, shift=bbmd.SHIFT_FORCE, skin=args.skin)
         sims = bbmd.Sim(ps, n, L, sp, None, None, T0=T_HIGH, seed=rank,
                         stream=stream.cuda_stream, use_torch_allocator=True)
         sims.step(200, DT, (bbmd.THERMO_NH, T_HIGH, 0.5, TAU))
@@ -369,7 +369,7 @@ def run_ours(args):
     hp_per = half_pairs_per_particle()
     flops_launch = n * hp_per * FLOP_PER_HALF_PAIR
     achieved = flops_launch / (force_ms / 1e3) / 1e12
-    traffic = force_traffic(n)
+    traffic = force_traffic(n, args.skin)
     out = {
         "metric": "particle-steps/s (binary LJ, 16M & 1.02B N) mixed vs FP64 GPU; % of roofline",
         "value": value,
@@ -399,7 +399,7 @@ def run_ours(args):
                      "algorithmic": f"{hp_per:.2f} half pairs/particle x {FLOP_PER_HALF_PAIR:.0f} "
                                     f"flop x {n} particles per launch",
                      "force_ms": force_ms,
-                     "issue": force_issue(n, force_ms, block_z, clock_mhz, nsm)},
+                     "issue": force_issue(n, force_ms, block_z, clock_mhz, nsm, args.skin)},
         "fma_probe": probe,
         "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
         "block_z": block_z,
@@ -574,10 +574,11 @@ def ctypes_sizeof_obs(bbmd):
     return ctypes.sizeof(bbmd.bbmd_obs)
 
 
-def force_counters():
+def force_counters(skin=None):
     """The committed ncu record of one list-mode k_force launch (DRAM bytes and warp
-    instructions per particle, block shape), or None when the kernel source changed since
-    those counters were taken."""
+    instructions per particle, block shape, skin), or None when the kernel source changed
+    since those counters were taken, or the record is of another skin (the list length
+    follows the skin)."""
     import hashlib
 
     tf = os.path.join(ROOT, "profiles", "force_traffic.json")
@@ -585,22 +586,24 @@ def force_counters():
     try:
         rec = json.load(open(tf))
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if skin is not None and abs(rec.get("skin", 0.3) - skin) > 1e-9:
+            return None
         return rec if rec.get("k_force_cu_sha1") == sha else None
     except Exception:
         return None
 
 
-def force_traffic(n):
+def force_traffic(n, skin=None):
     """DRAM bytes (read + write) per k_force launch, scaled to n particles (every array the
     kernel touches is per particle), or None."""
-    rec = force_counters()
+    rec = force_counters(skin)
     return rec["bytes_per_particle"] * n if rec else None
 
 
-def force_issue(n, force_ms, block_z, clock_mhz, nsm):
+def force_issue(n, force_ms, block_z, clock_mhz, nsm, skin=None):
     """Issue-slot view of the same launch: warp instructions (from the ncu record, same
     block shape) per second against 4 warp instructions per SM per cycle."""
-    rec = force_counters()
+    rec = force_counters(skin)
     if not rec or rec.get("block_z") != block_z or "warp_inst_per_particle" not in rec:
         return None
     peak = nsm * 4 * clock_mhz * 1e6
@@ -697,6 +700,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--skin", type=float, default=0.4,
+                    help="Verlet skin of the 16 M workload and its FP64 and soft-sphere legs "
+                         "(0.4: the fastest of 0.25-0.6 measured at 16 M; the 1.02 B cell-mode "
+                         "step keeps 0.3, its fastest)")
     ap.add_argument("--equil", type=int, default=400,
                     help="untimed equilibration steps at T=2.0 before the ramp")
     ap.add_argument("--fp64-steps", type=int, default=3)

@@ -53,6 +53,10 @@ def test_force_counters_follow_the_source(bench, tmp_path, monkeypatch):
     # 150e6 warp instructions in 1 ms against 152 SMs x 4 per cycle at 2 GHz
     assert issue["frac"] == pytest.approx(1.5e11 / (152 * 4 * 2e9))
     assert bench.force_issue(1_000_000, 1.0, 8, 2000.0, 152) is None  # another block shape
+    # a record without a skin is of the skin 0.3; another skin has other lists
+    assert bench.force_traffic(1000, 0.3) == pytest.approx(284000.0)
+    assert bench.force_traffic(1000, 0.4) is None
+    assert bench.force_issue(1_000_000, 1.0, 4, 2000.0, 152, 0.4) is None
     # any change of the source voids the record
     (tmp_path / "paper_1105_5613_gb300" / "csrc" / "k_force.cu").write_text(src + " ")
     assert bench.force_traffic(1000) is None

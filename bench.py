@@ -525,8 +525,8 @@ def run_replicas(args, stream):
     t_gen = time.perf_counter() - t0
     temps = [0.4 + 1.6 * r / max(R - 1, 1) for r in range(R)]
     t0 = time.perf_counter()
-    b = bbmd.Batch(bbmd.ka_params(), ns, boxes, sp, pos, None, T0=temps, seed=0,
-                   stream=stream.cuda_stream)
+    b = bbmd.Batch(bbmd.ka_params(skin=args.replica_skin), ns, boxes, sp, pos, None, T0=temps,
+                   seed=0, stream=stream.cuda_stream)
     for r in range(R):
         b.replica(r).minimize(200)
     stream.synchronize()
@@ -546,7 +546,7 @@ def run_replicas(args, stream):
     b.close()
     ntot = sum(ns)
     return {"workload": f"{R} replicas, N_r in [2048, 32768] (sum {ntot}), RSA + 200 SD steps, "
-                        "T_r = 0.4 .. 2.0, Nose-Hoover, dt=0.005, "
+                        f"T_r = 0.4 .. 2.0, Nose-Hoover, dt=0.005, skin {args.replica_skin}, "
                         + ("one persistent kernel launch per call (up to 1024 steps)"
                            if path == "persistent" else "one graph launch per step"),
             "path": path,
@@ -720,6 +720,9 @@ def main():
     ap.add_argument("--replicas", type=int, default=64,
                     help="number of replicas of the batched-replica leg (0 = skip)")
     ap.add_argument("--replica-steps", type=int, default=500)
+    ap.add_argument("--replica-skin", type=float, default=0.3,
+                    help="Verlet skin of the replicas (their boxes need 4 cells a side for the "
+                         "batch's 2 x 2 x 4 blocks)")
     ap.add_argument("--large-steps", type=int, default=20,
                     help="timed mixed-precision steps of the 1.02e9-particle cell-mode step")
     ap.add_argument("--large-untimed", type=int, default=5,

@@ -211,7 +211,13 @@ void bbmd_destroy(bbmd_sim* sim);
 
 /* Advance nsteps velocity-Verlet steps of size dt (Sec. 2.3.2) under the thermostat
  * (NULL = NVE).  Asynchronous: returns after enqueueing on the handle's stream.  The list
- * is rebuilt on the device when needed, without a host round trip. */
+ * is rebuilt on the device when needed, without a host round trip.
+ * The last step's closing half kick (and Nose-Hoover scale) is left pending in the stored
+ * velocities: the next call with the same dt applies it within its first velocity update,
+ * as two steps of one call do (so split calls give the trajectory of one call, bit for
+ * bit); a call with another dt, bbmd_get_state, bbmd_set_state, bbmd_minimize, bbmd_tune
+ * and bbmd_rebuild apply it first; bbmd_observe reports the finished velocities' kinetic
+ * energy and momentum without storing them. */
 bbmd_status bbmd_step(bbmd_sim* sim, int64_t nsteps, double dt, const bbmd_thermostat* thermo);
 
 /* Phases timed by bbmd_step_profiled. */

@@ -60,8 +60,10 @@ __global__ void k_begin(DevSim s, int64_t nsteps, double dt, int kind, double T0
     sc->s_end = 1.0;
 }
 
+// Four CTAs per SM (64 registers; the compiler would take 92 and fit two): the kernel is
+// bound by HBM, and more resident warps keep more of its loads in flight.
 template <bool FP64>
-__global__ void __launch_bounds__(kThreads) k_integrate(DevSim s) {
+__global__ void __launch_bounds__(kThreads, 4) k_integrate(DevSim s) {
     integrate_body<FP64>(s, (int)blockIdx.x, (int)gridDim.x);
 }
 
@@ -69,7 +71,7 @@ BBMD_ONE_AND_MANY(kThreads, k_celltop, celltop_body)
 BBMD_ONE_AND_MANY(kThreads, k_check, check_body)
 
 template <bool FP64>
-__global__ void __launch_bounds__(kThreads) k_integrate_many(ManySims m) {
+__global__ void __launch_bounds__(kThreads, 4) k_integrate_many(ManySims m) {
     __shared__ DevSim sh;
     int lb, lg;
     load_replica(m, sh, lb, lg);

@@ -55,6 +55,11 @@
 #ifndef BBMD_FORCE_MIN_BLOCKS
 #define BBMD_FORCE_MIN_BLOCKS BBMD_SHAPE_FORCE_MIN
 #endif
+// the stencil (cell-mode) force kernel of a 2 x 2 x 4 block fits three CTAs per SM in
+// shared memory; bounded to them it compiles to 80 registers
+#ifndef BBMD_CELL_MIN_BLOCKS
+#define BBMD_CELL_MIN_BLOCKS (BBMD_BLOCK_Z == 4 ? 3 : BBMD_FORCE_MIN_BLOCKS)
+#endif
 #ifndef BBMD_LIST_MIN_BLOCKS
 #define BBMD_LIST_MIN_BLOCKS BBMD_SHAPE_LIST_MIN
 #endif
@@ -1547,12 +1552,14 @@ __device__ __forceinline__ void force64_body(const DevSim& s, int lb, int lg) {
 // a batch that owns the CTA.
 
 template <int MODE, bool KE, bool FSHIFT>
-__global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force(DevSim s) {
+__global__ void __launch_bounds__(kBW * 32, MODE == 1 ? BBMD_CELL_MIN_BLOCKS : BBMD_FORCE_MIN_BLOCKS)
+    k_force(DevSim s) {
     force_body<MODE, KE, FSHIFT>(s, (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <int MODE, bool KE, bool FSHIFT>
-__global__ void __launch_bounds__(kBW * 32, BBMD_FORCE_MIN_BLOCKS) k_force_many(ManySims m) {
+__global__ void __launch_bounds__(kBW * 32, MODE == 1 ? BBMD_CELL_MIN_BLOCKS : BBMD_FORCE_MIN_BLOCKS)
+    k_force_many(ManySims m) {
     __shared__ DevSim sh;
     int lb, lg;
     load_replica(m, sh, lb, lg);
@@ -1690,6 +1697,8 @@ int force_blocks_per_sm(const DevSim& s) {
                                                  : kStageBuffers * (size_t)(s.smax + 1) * sizeof(float4);
     if (s.precision == BBMD_PREC_FP64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force64<0, false, true, false>, kBW * 32, bytes);
+    else if (s.nbr_mode == BBMD_NBR_CELL)  // the stencil kernel is the step's force kernel
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force<1, true, false>, kBW * 32, bytes);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force<0, true, false>, kBW * 32, bytes);
     return nb > 0 ? nb : 1;

@@ -346,11 +346,19 @@ bbmd_status bbmd_batch_set_branches(bbmd_batch* b, int32_t branches);
  * phase after phase; an item starts once its replica's previous phase has finished, so
  * the phases and steps of different replicas overlap.  It applies to mixed precision with
  * block shape 2 x 2 x 4 (the batch default) on a device with cooperative launch;
- * otherwise bbmd_step_batch returns BBMD_ERR_STATE.  A wait gives up after a second; the
- * replicas then report BBMD_ERR_TIMEOUT at their next synchronising call.  GRAPH: one
- * CUDA graph launch per step (bbmd_batch_set_branches). */
+ * otherwise bbmd_step_batch returns BBMD_ERR_STATE.  A wait gives up after a second
+ * (bbmd_batch_set_wait_limit); the replicas then report BBMD_ERR_TIMEOUT at their next
+ * synchronising call.  GRAPH: one CUDA graph launch per step (bbmd_batch_set_branches). */
 enum { BBMD_BATCH_AUTO = 0, BBMD_BATCH_GRAPH = 1, BBMD_BATCH_PERSISTENT = 2 };
 bbmd_status bbmd_batch_set_mode(bbmd_batch* b, int32_t mode);
+
+/* Limit of each dependency wait of the persistent step, in ns (default 1e9; ns >= 1, else
+ * BBMD_ERR_ARG).  A wait that runs out raises an abort flag: every CTA of the launch
+ * returns at its next work item, the rest of the call's launches return at once, and
+ * every replica reports BBMD_ERR_TIMEOUT at its next synchronising call.  The replicas'
+ * states are then those of partly completed steps (destroy the batch); the device context
+ * stays usable.  The paper has no counterpart (failure detection of this design). */
+bbmd_status bbmd_batch_set_wait_limit(bbmd_batch* b, uint64_t ns);
 
 /* 1 if the next bbmd_step_batch takes the persistent step, else 0. */
 int32_t bbmd_batch_uses_persistent(const bbmd_batch* b);

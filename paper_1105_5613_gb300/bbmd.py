@@ -91,7 +91,7 @@ EXPORTS = ["bbmd_create", "bbmd_destroy", "bbmd_step", "bbmd_step_profiled", "bb
            "bbmd_get_neighbors", "bbmd_rebuild", "bbmd_get_info", "bbmd_last_error",
            "bbmd_gr_counts_noalloc", "bbmd_tune", "bbmd_get_forces_ids", "bbmd_create_batch", "bbmd_step_batch",
            "bbmd_batch_replica", "bbmd_batch_size", "bbmd_batch_set_branches",
-           "bbmd_batch_set_mode", "bbmd_batch_uses_persistent",
+           "bbmd_batch_set_mode", "bbmd_batch_set_wait_limit", "bbmd_batch_uses_persistent",
            "bbmd_destroy_batch",
            "bbmd_batch_last_error", "bbmd_fma_peak", "bbmd_smem_scatter_rate"]
 
@@ -156,6 +156,8 @@ def load(path: str | None = None):
     L.bbmd_batch_set_branches.restype = C.c_int
     L.bbmd_batch_set_mode.argtypes = [vp, C.c_int32]
     L.bbmd_batch_set_mode.restype = C.c_int
+    L.bbmd_batch_set_wait_limit.argtypes = [vp, C.c_uint64]
+    L.bbmd_batch_set_wait_limit.restype = C.c_int
     L.bbmd_batch_uses_persistent.argtypes = [vp]
     L.bbmd_batch_uses_persistent.restype = C.c_int32
     L.bbmd_batch_size.argtypes = [vp]
@@ -505,6 +507,13 @@ class Batch:
         rc = load().bbmd_batch_set_mode(self.h, int(mode))
         if rc != BBMD_OK:
             raise BBMDError(rc, "bbmd_batch_set_mode")
+
+    def set_wait_limit(self, ns):
+        """Limit of each dependency wait of the persistent step, in ns
+        (bbmd_batch_set_wait_limit)."""
+        rc = load().bbmd_batch_set_wait_limit(self.h, int(ns))
+        if rc != BBMD_OK:
+            raise BBMDError(rc, "bbmd_batch_set_wait_limit")
 
     def uses_persistent(self):
         return bool(load().bbmd_batch_uses_persistent(self.h))

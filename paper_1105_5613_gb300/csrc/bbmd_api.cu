@@ -1208,6 +1208,7 @@ struct bbmd_batch {
     size_t pctl_bytes = 0;           // bytes of head + finished counts (cleared every launch)
     int pgrid = 0, psmax = 0;
     std::vector<int> pgen;           // replicas' graph generations at the table upload
+    uint64_t wait_ns = 1000000000ull;  // dependency-wait limit of the persistent step
 };
 
 namespace {
@@ -1605,6 +1606,7 @@ bbmd_status bbmd_step_batch(bbmd_batch* b, int64_t nsteps, double dt, const bbmd
         for (int64_t k = 0; k < nsteps; k += per_launch) {
             PersistentStep a = b->pst;
             a.nsteps = (int32_t)std::min<int64_t>(per_launch, nsteps - k);
+            a.wait_ns = b->wait_ns;
             cudaError_t e = cudaMemsetAsync(b->pctl, 0, b->pctl_bytes, b->st);
             if (e == cudaSuccess)
                 e = BBMD_PERSIST_NS::launch_persistent_step(a, b->pgrid, b->psmax, nh != 0, fshift, b->st);
@@ -1648,6 +1650,12 @@ bbmd_status bbmd_batch_set_mode(bbmd_batch* b, int32_t mode) {
 int32_t bbmd_batch_uses_persistent(const bbmd_batch* b) {
     if (!b) return 0;
     return b->mode != BBMD_BATCH_GRAPH && persistent_eligible(b) ? 1 : 0;
+}
+
+bbmd_status bbmd_batch_set_wait_limit(bbmd_batch* b, uint64_t ns) {
+    if (!b || ns == 0) return BBMD_ERR_ARG;
+    b->wait_ns = ns;
+    return BBMD_OK;
 }
 
 bbmd_status bbmd_batch_set_branches(bbmd_batch* b, int32_t branches) {

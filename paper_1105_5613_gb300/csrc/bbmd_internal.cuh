@@ -307,6 +307,7 @@ struct PersistentStep {
     int32_t* abort;           // raised when a wait gives up (stays raised for the call)
     int32_t nrep, nitems;     // replicas; work items of one step
     int32_t nsteps;           // steps of this launch (items nitems * nsteps)
+    uint64_t wait_ns;         // a dependency wait gives up after this many ns
 };
 #define BBMD_PERSIST_NS2(n) z##n
 #define BBMD_PERSIST_NS1(n) BBMD_PERSIST_NS2(n)

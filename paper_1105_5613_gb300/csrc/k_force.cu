@@ -1262,8 +1262,6 @@ __device__ __forceinline__ void list_build_body(const DevSim& s, int lb, int lg)
 #include "sort_bodies.cuh"
 #include "step_bodies.cuh"
 
-constexpr unsigned long long kWaitNs = 1000000000ull;  // a dependency wait gives up after 1 s
-
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1328,7 +1326,7 @@ __global__ void __launch_bounds__(kBW * 32, 2) k_step_persistent(PersistentStep 
                                 d.x = -1;
                                 break;
                             }
-                            if (globaltimer_ns() - t0 > kWaitNs) {
+                            if (globaltimer_ns() - t0 > a.wait_ns) {
                                 persistent_abort(a);
                                 d.x = -1;
                                 break;

@@ -130,3 +130,37 @@ def test_batch_argument_errors():
     with pytest.raises(bbmd.BBMDError):  # a replica whose box holds fewer than 3 cells
         bbmd.Batch(bbmd.ka_params(), [4000, 500], [gen.box_for(4000, 1.2), gen.box_for(500, 1.2)],
                    [np.zeros(4000, np.uint8), np.zeros(500, np.uint8)])
+
+
+def test_persistent_wait_that_runs_out_reports_timeout():
+    """Failure detection without a GPU fault.  With a dependency-wait limit of 1 ns, the
+    first wait of the persistent step that is not met at once gives up: the launch aborts,
+    every replica reports BBMD_ERR_TIMEOUT at its next synchronising call, and the device
+    stays usable (a new batch then steps like the oracle)."""
+    ms, temps = [8, 9, 10, 11], [0.5, 1.0, 1.5, 2.0]
+    ns, boxes, pos, vel, sp = lattice_replicas(ms, temps)
+    p = bbmd.ka_params()
+    th = [(bbmd.THERMO_NH, T, T, 0.5) for T in temps]
+    b = bbmd.Batch(p, ns, boxes, sp, pos, vel)
+    assert b.uses_persistent()
+    with pytest.raises(bbmd.BBMDError) as e:
+        b.set_wait_limit(0)
+    assert e.value.code == 1  # BBMD_ERR_ARG
+    b.set_wait_limit(1)
+    b.step(20, 0.005, th)  # asynchronous: the status is read by the next synchronising call
+    for r in range(len(ns)):
+        with pytest.raises(bbmd.BBMDError) as e:
+            b.replica(r).observe(0)
+        assert e.value.code == 7, r  # BBMD_ERR_TIMEOUT
+    b.close()
+    b = bbmd.Batch(p, ns, boxes, sp, pos, vel)
+    assert b.uses_persistent()
+    b.step(20, 0.005, th)
+    for r in range(len(ns)):
+        xq, _, _ = quantized(pos[r], boxes[r])
+        st = oracle.MDState(xq, vel[r], sp[r], boxes[r], oracle_params(p))
+        oracle.md_run(st, 20, 0.005, thermo=th[r][1:], use_cells=True)
+        gp, _, _ = b.replica(r).get_state()
+        assert min_image_rms(gp, st.pos, boxes[r]) <= 1e-4, r
+        assert b.replica(r).observe(0)["step"] == 20
+    b.close()

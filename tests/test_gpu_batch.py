@@ -1,7 +1,8 @@
 """Replica batches (bbmd_create_batch / bbmd_step_batch): every replica of a batch against
 the oracle on its own generated inputs, at its own temperature; the persistent step (one
 cooperative launch per step) and the batch graph both equal, bit for bit, to stepping
-each replica handle on its own; argument errors."""
+each replica handle on its own; argument errors; a persistent-step wait that runs out
+(BBMD_ERR_TIMEOUT on every replica, the device usable after)."""
 import numpy as np
 import pytest
 
